@@ -1,0 +1,198 @@
+/*
+ * glasso.h -- C ABI of libglasso, a GB300 (sm_103a) solver for the graphical lasso
+ *
+ *     min_{Theta > 0}  F(Theta) = -log det Theta + tr(S Theta) + lambda * ||Theta||_1
+ *
+ * (Sec. 3.1 of Shalom, Treister & Yavneh, "pISTA: preconditioned Iterative Soft
+ * Thresholding Algorithm for Graphical Lasso", eq. sparse_obj; ||.||_1 sums all n*n
+ * entries, the diagonal included) by pISTA (Sec. 4, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are dense, row-major, n x n with leading dimension n.  S and Theta are
+ *     symmetric; the library reads the LOWER triangle of S and mirrors it.
+ *   - Ownership: the caller owns every pointer it passes and every output buffer; the
+ *     library owns the handle and all device state behind it.  Nothing passed in is
+ *     retained after a call returns (glasso_submit copies S before it returns).
+ *   - Errors: every call returns a glasso_status; nothing throws across the ABI.  On an
+ *     error the outputs are unspecified and glasso_last_error(h) describes the cause.
+ *   - Threading: one handle serves one host thread at a time, except that glasso_submit
+ *     and glasso_poll may be called from any thread while the serving loop runs.
+ *   - GLASSO_ERR_CUDA means a CUDA call failed; the handle should then be destroyed.
+ *   - All work runs on the handle's stream; calls return after that work has finished.
+ */
+#ifndef GLASSO_H
+#define GLASSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GLASSO_OK = 0,
+  GLASSO_ERR_ARG = 1,            /* invalid argument (n < 1, lambda <= 0, tol < 0, NULL ...) */
+  GLASSO_ERR_NOT_SYMMETRIC = 2,  /* |S_ij - S_ji| > 1e-12 * max|S| */
+  GLASSO_ERR_NONFINITE = 3,      /* S holds NaN or Inf, or some S_ii < 0 */
+  GLASSO_ERR_NOT_PD = 4,         /* the start point Theta0 (or the op input) is not PD */
+  GLASSO_ERR_OOM = 5,            /* a device or pinned-host allocation failed */
+  GLASSO_ERR_BUDGET = 6,         /* the problem cannot fit the configured HBM budget */
+  GLASSO_ERR_CUDA = 7,           /* a CUDA runtime / driver call failed */
+  GLASSO_ERR_TIMEOUT = 8,        /* a bounded wait ran out */
+  GLASSO_MAX_ITER = 9,           /* stopped at max_iter; the result is the last PD iterate */
+  GLASSO_LINESEARCH_STALL = 10,  /* no step passed the line search; the result is the last
+                                    PD iterate (Sec. 4.3.2, Sec. 6 fallback step) */
+  GLASSO_PENDING = 11,           /* glasso_poll: the request has not finished yet */
+  GLASSO_ERR_UNSUPPORTED = 12    /* the device is not an sm_103 GPU, or the mode is absent */
+} glasso_status;
+
+typedef enum {
+  GLASSO_FP64 = 0,          /* every step in FP64 */
+  GLASSO_MIXED_TF32X3 = 1,  /* dense products on the tensor cores with 3-term TF32 splits;
+                               FP64 Cholesky panels, FP64-refined W, FP64 decisions */
+  GLASSO_MIXED_BF16X3 = 2   /* as GLASSO_MIXED_TF32X3 with 3-term BF16 splits */
+} glasso_precision;
+
+typedef enum { GLASSO_F64 = 0, GLASSO_F32 = 1 } glasso_dtype;
+typedef enum { GLASSO_HOST = 0, GLASSO_DEVICE = 1 } glasso_memory;
+
+typedef struct glasso_handle glasso_handle;
+
+typedef struct {
+  int device;               /* CUDA ordinal */
+  void* stream;             /* cudaStream_t to run on; NULL: the library creates its own */
+  glasso_precision precision;
+  int max_iter;             /* default 500 */
+  double shrink;            /* line-search factor; default 0.5 (Sec. 4.3.2 leaves it open) */
+  double t_min;             /* halving stops below this t; default 1e-4 (Sec. 6) */
+  size_t hbm_budget_bytes;  /* device memory the handle may hold; 0 = no limit */
+  int serve_slots;          /* requests the serving loop runs at once; default 8 */
+} glasso_config;
+
+typedef struct {
+  int32_t status;           /* glasso_status of this solve */
+  int32_t iterations;       /* accepted pISTA iterations */
+  int32_t trials;           /* line-search trials (Cholesky factorisations of trial points) */
+  int32_t nnz;              /* nonzeros of Theta over all n*n entries */
+  double rel_kkt_l1;        /* ||Z||_1 / ||Theta||_1, Z the minimum-norm sub-gradient (Sec. 6) */
+  double min_subgrad_fro;   /* ||Z||_F */
+  double objective;         /* F(Theta), eq. sparse_obj */
+  double logdet;            /* log det Theta */
+  double seconds;           /* wall time of the solve inside the library */
+  double t_submit, t_start, t_done;  /* serving timestamps (s, monotonic clock), else 0 */
+} glasso_result;
+
+/* ---- handle ------------------------------------------------------------------------------ */
+
+/* Fill *cfg with the defaults listed above (device 0, own stream, FP64). */
+glasso_status glasso_config_default(glasso_config* cfg);
+
+/* Create a handle for cfg->device (NULL cfg: defaults).  GLASSO_ERR_UNSUPPORTED when the
+ * device is not compute capability 10.3.  *out is set to the handle, or NULL on error. */
+glasso_status glasso_create(const glasso_config* cfg, glasso_handle** out);
+
+/* Stop the serving loop (unfinished requests are dropped), free all device memory and
+ * the handle.  NULL is accepted. */
+glasso_status glasso_destroy(glasso_handle* h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char* glasso_last_error(const glasso_handle* h);
+
+/* Name of a status code. */
+const char* glasso_status_string(glasso_status s);
+
+/* ---- solve (Algorithm 1) ------------------------------------------------------------------ */
+
+/* One pISTA solve of the graphical lasso for (S, lambda), stopped when
+ * ||Z||_1 <= tol * ||Theta||_1 (Sec. 6 stop rule, checked before each direction).
+ *   S        n x n, dtype s_dtype (FP32 is promoted exactly to FP64), in host or device
+ *            memory as `where` says.
+ *   theta0   optional start point (FP64, same memory kind as S); NULL: the start point of
+ *            Sec. 6, diag(1/(S_ii + lambda)).  Must be symmetric positive definite.
+ *   theta_out  n x n FP64 output (same memory kind as S), may be NULL.
+ *   res      optional summary.
+ * Returns GLASSO_OK on convergence, GLASSO_MAX_ITER / GLASSO_LINESEARCH_STALL with the last
+ * (positive-definite) iterate in theta_out, or an error. */
+glasso_status glasso_solve(glasso_handle* h, const void* S, glasso_dtype s_dtype,
+                           glasso_memory where, int64_t n, double lambda, double tol,
+                           const double* theta0, double* theta_out, glasso_result* res);
+
+/* ---- batched regularisation paths -------------------------------------------------------- */
+
+typedef struct {
+  int64_t n;
+  const void* S;            /* host memory, n x n, dtype below */
+  glasso_dtype dtype;
+  int32_t n_lambda;
+  const double* lambdas;    /* n_lambda values, solved in DESCENDING order, each warm-started
+                               from the previous solution of the same problem */
+  double tol;
+  double* theta_out;        /* host, n_lambda * n * n FP64 (in the order given), or NULL */
+} glasso_problem;
+
+/* Solve `count` independent problems, each along its lambda path.  Problems run
+ * concurrently on the device.  results: count * n_lambda entries, problem-major, in the
+ * order the lambdas were given.  Returns the first error met, else GLASSO_OK (per-solve
+ * convergence is in results[].status). */
+glasso_status glasso_solve_batch(glasso_handle* h, const glasso_problem* probs, int32_t count,
+                                 glasso_result* results);
+
+/* ---- serving (continuous batching) ------------------------------------------------------- */
+
+typedef struct {
+  int64_t n;
+  const void* S;            /* host memory, copied before glasso_submit returns */
+  glasso_dtype dtype;
+  double lambda;
+  double tol;
+  int64_t dataset_id;       /* requests with the same id share S; the solution of the nearest
+                               earlier lambda for the id warm-starts the solve; -1: none */
+} glasso_request;
+
+/* Queue a request; returns at once with *ticket.  Requests are admitted while their device
+ * memory fits hbm_budget_bytes and a slot is free, and run concurrently with the requests
+ * already on the device.  GLASSO_ERR_BUDGET if the request can never fit. */
+glasso_status glasso_submit(glasso_handle* h, const glasso_request* req, uint64_t* ticket);
+
+/* GLASSO_PENDING while the request runs; otherwise its final status, with *res filled and,
+ * if theta_out is not NULL, the n x n FP64 solution copied to host memory.  A finished
+ * ticket can be polled once; GLASSO_ERR_ARG for an unknown ticket. */
+glasso_status glasso_poll(glasso_handle* h, uint64_t ticket, glasso_result* res,
+                          double* theta_out);
+
+/* ---- single steps on device memory (one pISTA step each, for testing and composition) ---- */
+/* All pointers are device pointers to n x n row-major FP64 arrays (code: int8) with leading
+ * dimension n; the step runs in the handle's precision mode and returns when done. */
+
+/* Cholesky factor A = L L^T (lower L, upper triangle of L set to 0), *pd = 1 if A is
+ * positive definite (every pivot finite and > 0), log det A = 2 sum log L_ii (Sec. 4.3.2,
+ * eq. t_cond_pd and the objective of eq. sparse_obj). */
+glasso_status glasso_op_cholesky(glasso_handle* h, const double* A, int64_t n, double* L,
+                                 int32_t* pd, double* logdet);
+
+/* W = A^{-1} (eq. grad_hessian needs it) for a symmetric positive-definite A, from the
+ * Cholesky factor: W = L^{-T} L^{-1}.  GLASSO_ERR_NOT_PD if A is not PD. */
+glasso_status glasso_op_inverse(glasso_handle* h, const double* A, int64_t n, double* W);
+
+/* From (S, A, W = A^{-1}): g = S - W (eq. grad_hessian), free set M (eqs. free_set, M),
+ * sign guess G (eq. G+), X = (g + lambda G) . M, which is the minimum-norm sub-gradient Z,
+ * and code = G . M in {-1, 0, 1}.  sums[0..3] = ||Z||_1, ||A||_1, ||Z||_F^2, nnz(A). */
+glasso_status glasso_op_gradient(glasso_handle* h, const double* S, const double* A,
+                                 const double* W, int64_t n, double lambda, double* X,
+                                 int8_t* code, double sums[4]);
+
+/* Y = A X A for symmetric A, X (the two triple products of eq. b, fused). */
+glasso_status glasso_op_sandwich(glasso_handle* h, const double* A, const double* X, int64_t n,
+                                 double* Y);
+
+/* Trial point A_t = A + M . D with D = -A + ST(A - tB, tC) (eq. d_sol), where
+ * B = Y - C . code (eq. b), C from eq. c, and M = (code != 0). */
+glasso_status glasso_op_trial(glasso_handle* h, const double* A, const double* Y,
+                              const int8_t* code, int64_t n, double lambda, double t,
+                              double* At);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

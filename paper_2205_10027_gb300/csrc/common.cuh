@@ -1,0 +1,86 @@
+// Shared definitions of the libglasso CUDA sources (device helpers, launch checks).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <cmath>
+
+namespace glasso {
+
+// Every dense n x n operand is stored padded to np = round_up(n, kPad) rows and columns
+// with leading dimension np.  The padded block of Theta is the identity, so products,
+// factorisations and log-dets of the padded matrices equal those of the n x n ones.
+constexpr int kPad = 128;
+// Width of the Cholesky panel / diagonal blocks whose inverses the factorisation keeps.
+constexpr int kNb = 64;
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Scalars the line search and stop test read back, one struct per solve.  Each field is
+// written by exactly one kernel.
+struct Scalars {
+  double z_l1, a_l1, z_fro2, nnz;      // gradient pass
+  double lin_s, lin_l1;                // trial pass: <S, dA> and sum(|At| - |A|)
+  double trsa_t, l1_t, nnz_t;          // trial pass: tr(S At), ||At||_1, nnz(At)
+  double logdet_t;                     // Cholesky of the trial point
+  int32_t pd_t;                        // 1 while the trial factorisation has met no bad pivot
+  int32_t pad0;
+  double tr_e, tr_e2;                  // second-order log-det difference (tier 2)
+  double trsa, l1;                     // objective pieces of a given matrix
+  double aux[8];
+};
+
+// Deterministic block reduction: every block writes its partial sums; one block then
+// adds them in index order.  kRedBlocks partials per quantity.
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the block (blockDim.x a multiple of 32, <= 1024); the result is valid in
+// thread 0.  Fixed order: lanes by xor-butterfly, then warps in index order.
+__device__ __forceinline__ double block_sum(double v, double* smem32) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem32[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) s += smem32[w];
+  }
+  return s;
+}
+
+__device__ __forceinline__ double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+// SoftThreshold(v, c) = sign(v) max(|v| - c, 0)  (App. A.1).
+__device__ __forceinline__ double soft_threshold(double v, double c) {
+  const double m = fabs(v) - c;
+  return m > 0.0 ? copysign(m, v) : 0.0;
+}
+
+}  // namespace glasso
+
+#include <stdexcept>
+#include <string>
+namespace glasso {
+// Host code reports failures by throwing Error; the C ABI turns it into a status code.
+struct Error : std::runtime_error {
+  int status;
+  Error(int st, const std::string& m) : std::runtime_error(m), status(st) {}
+};
+}  // namespace glasso
+
+// GLASSO_ERR_CUDA = 7 in glasso.h
+#define CUDA_CHECK(expr)                                                                 \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      throw ::glasso::Error(7, std::string(#expr) + ": " + cudaGetErrorString(_e) +      \
+                                   " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+  } while (0)
+#define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())

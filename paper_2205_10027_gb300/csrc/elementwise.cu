@@ -1,0 +1,429 @@
+// HBM-bound passes of the pISTA iteration.  Every pass reads and writes each n x n entry
+// at most once, in 128-bit (or coalesced 32 x 32-tile) accesses, and reduces the scalars
+// the host needs into per-block partial sums that one block then adds in a fixed order
+// (results do not depend on scheduling).
+#include "elementwise.h"
+
+namespace glasso {
+
+namespace {
+constexpr int RT = kRedThreads;  // 256
+
+// lower-triangle tile index t -> (bi, bj), bi >= bj, t = bi (bi + 1) / 2 + bj
+__device__ __forceinline__ void tri_tile(int64_t t, int& bi, int& bj) {
+  int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  bi = (int)i;
+  bj = (int)(t - i * (i + 1) / 2);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// ---- S: copy the lower triangle of the caller's n x n S into the padded FP64 buffer,
+//      mirrored, and record max |S_ij - S_ji|, max |S_ij|, non-finite count, min S_ii.
+template <typename T>
+__global__ void k_load_sym(const T* __restrict__ src, int64_t n, double* __restrict__ dst,
+                           int64_t ld, int np, double* vmax /*[2]*/, int* bad) {
+  __shared__ double lo[32][33], up[32][33];
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  double asym = 0.0, amax = 0.0;
+  int nbad = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int bi, bj;
+    tri_tile(t, bi, bj);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = bi * 32 + r, j = bj * 32 + tx;   // tile (bi, bj): row i, col j
+      const int64_t i2 = bj * 32 + r, j2 = bi * 32 + tx;  // tile (bj, bi)
+      lo[r][tx] = (i < n && j < n) ? (double)src[i * n + j] : 0.0;
+      up[r][tx] = (i2 < n && j2 < n) ? (double)src[i2 * n + j2] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = bi * 32 + r, j = bj * 32 + tx;
+      // lower entry (i, j) = lo[r][tx]; its mirror (j, i) is up[tx][r]
+      if (i < n && j < n && j <= i) {
+        const double a = lo[r][tx], b = up[tx][r];
+        if (!isfinite(a) || !isfinite(b)) ++nbad;
+        else {
+          asym = fmax(asym, fabs(a - b));
+          amax = fmax(amax, fabs(a));
+          if (i == j && a < 0.0) ++nbad;
+        }
+      }
+      dst[i * ld + j] = (j <= i) ? lo[r][tx] : lo[tx][r];
+      const int64_t i2 = bj * 32 + r, j2 = bi * 32 + tx;  // upper tile gets the transpose
+      if (bi != bj) dst[i2 * ld + j2] = lo[tx][r];
+    }
+  }
+  if (asym > 0.0) atomic_max_nonneg(&vmax[0], asym);
+  if (amax > 0.0) atomic_max_nonneg(&vmax[1], amax);
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+// ---- start point A0 = diag(1/(S_ii + lam)), identity on the padding (Sec. 6)
+__global__ void k_init_diag(const double* S, int64_t ld, int64_t n, int np, double lam, double* A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  A[i * ld + i] = (i < n) ? 1.0 / (S[i * ld + i] + lam) : 1.0;
+}
+
+// ---- identity on the padded diagonal (i >= n) of an otherwise prepared matrix
+__global__ void k_pad_identity(double* A, int64_t ld, int64_t n, int np) {
+  const int64_t i = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < np) A[i * ld + i] = 1.0;
+}
+
+// ---- K1: g = S - W; free set; sign guess; X = (g + lam G).M (= minimum-norm sub-gradient Z);
+//      code = G.M; partial sums of |Z|, |A|, Z^2, [A != 0]
+__global__ void __launch_bounds__(RT) k_gradient(const double* __restrict__ S,
+                                                 const double* __restrict__ W,
+                                                 const double* __restrict__ A, int64_t ld,
+                                                 int64_t n, double lam, double* __restrict__ X,
+                                                 int8_t* __restrict__ code, int64_t ldc,
+                                                 double* __restrict__ parts) {
+  __shared__ double red[32];
+  double s_z = 0.0, s_a = 0.0, s_z2 = 0.0, s_nz = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double2* s2 = reinterpret_cast<const double2*>(S + i * ld);
+    const double2* w2 = reinterpret_cast<const double2*>(W + i * ld);
+    const double2* a2 = reinterpret_cast<const double2*>(A + i * ld);
+    double2* x2 = reinterpret_cast<double2*>(X + i * ld);
+    char2* c2 = reinterpret_cast<char2*>(code + i * ldc);
+    for (int64_t jp = threadIdx.x; 2 * jp < n; jp += blockDim.x) {
+      const double2 sv = s2[jp], wv = w2[jp], av = a2[jp];
+      double xs[2];
+      signed char cs[2];
+      const double ss[2] = {sv.x, sv.y}, ws[2] = {wv.x, wv.y}, as[2] = {av.x, av.y};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool valid = 2 * jp + h < n;
+        const double g = ss[h] - ws[h], a = as[h];
+        const bool in_m = (a != 0.0) || (fabs(g) > lam);
+        const double G = (a != 0.0) ? sgn(a) : -sgn(g);
+        const double x = in_m ? g + lam * G : 0.0;
+        xs[h] = valid ? x : 0.0;
+        cs[h] = (valid && in_m) ? (signed char)G : 0;
+        if (valid) {
+          s_z += fabs(x);
+          s_a += fabs(a);
+          s_z2 += x * x;
+          s_nz += (a != 0.0) ? 1.0 : 0.0;
+        }
+      }
+      x2[jp] = make_double2(xs[0], xs[1]);
+      c2[jp] = make_char2(cs[0], cs[1]);
+    }
+  }
+  const double t0 = block_sum(s_z, red);
+  const double t1 = block_sum(s_a, red);
+  const double t2 = block_sum(s_z2, red);
+  const double t3 = block_sum(s_nz, red);
+  if (threadIdx.x == 0) {
+    double* p = parts + (int64_t)blockIdx.x * 4;
+    p[0] = t0; p[1] = t1; p[2] = t2; p[3] = t3;
+  }
+}
+
+// ---- K3: trial point At = A + M.D, D = -A + ST(A - tB, tC), B = Y - C.code (eqs. b, c,
+//      d_sol); writes At in full and its lower triangle into Lt (the Cholesky input);
+//      partial sums of <S, dA>, sum(|At| - |A|), tr(S At), ||At||_1, nnz(At)
+__global__ void __launch_bounds__(RT) k_trial(const double* __restrict__ A,
+                                              const double* __restrict__ Y,
+                                              const int8_t* __restrict__ code, int64_t ldc,
+                                              const double* __restrict__ S, int64_t ld,
+                                              int64_t n, int np, double lam, double t,
+                                              double* __restrict__ At, double* __restrict__ Lt,
+                                              double* __restrict__ parts) {
+  __shared__ double tile[32][33];
+  __shared__ double red[32];
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  double s_lin = 0.0, s_l1d = 0.0, s_tr = 0.0, s_l1 = 0.0, s_nz = 0.0;
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int bi, bj;
+    tri_tile(tt, bi, bj);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+      double at;
+      if (i < n && j < n) {
+        const double a = A[i * ld + j];
+        const int cd = code[i * ldc + j];
+        at = a;
+        if (cd != 0 && j <= i) {
+          const double di = A[i * ld + i], dj = A[j * ld + j];
+          const double C = (i == j) ? lam * di * di : lam * (di * dj + a * a);
+          const double b = Y[i * ld + j] - C * (double)cd;
+          at = soft_threshold(a - t * b, t * C);
+        }
+        if (j <= i) {
+          const double s = S[i * ld + j], w = (i == j) ? 1.0 : 2.0;
+          s_lin += w * s * (at - a);
+          s_l1d += w * (fabs(at) - fabs(a));
+          s_tr += w * s * at;
+          s_l1 += w * fabs(at);
+          s_nz += (at != 0.0) ? w : 0.0;
+        }
+      } else {
+        at = (i == j) ? 1.0 : 0.0;  // identity padding
+      }
+      tile[r][tx] = at;
+      if (j <= i) {
+        At[i * ld + j] = at;
+        Lt[i * ld + j] = at;
+      }
+    }
+    __syncthreads();
+    if (bi != bj) {
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t i = (int64_t)bj * 32 + r, j = (int64_t)bi * 32 + tx;
+        At[i * ld + j] = tile[tx][r];
+      }
+    } else {
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+        if (j > i) At[i * ld + j] = tile[tx][r];
+      }
+    }
+  }
+  const double v0 = block_sum(s_lin, red);
+  const double v1 = block_sum(s_l1d, red);
+  const double v2 = block_sum(s_tr, red);
+  const double v3 = block_sum(s_l1, red);
+  const double v4 = block_sum(s_nz, red);
+  if (threadIdx.x == 0) {
+    double* p = parts + (int64_t)blockIdx.x * 5;
+    p[0] = v0; p[1] = v1; p[2] = v2; p[3] = v3; p[4] = v4;
+  }
+}
+
+// ---- tr(S A) and ||A||_1 of a full matrix
+__global__ void __launch_bounds__(RT) k_objective_terms(const double* __restrict__ S,
+                                                        const double* __restrict__ A, int64_t ld,
+                                                        int64_t n, double* __restrict__ parts) {
+  __shared__ double red[32];
+  double s_tr = 0.0, s_l1 = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double a = A[i * ld + j];
+      s_tr += S[i * ld + j] * a;
+      s_l1 += fabs(a);
+    }
+  const double v0 = block_sum(s_tr, red);
+  const double v1 = block_sum(s_l1, red);
+  if (threadIdx.x == 0) {
+    parts[(int64_t)blockIdx.x * 2] = v0;
+    parts[(int64_t)blockIdx.x * 2 + 1] = v1;
+  }
+}
+
+// ---- out[q] = sum_b parts[b * nq + q], fixed order
+__global__ void k_finalize(const double* __restrict__ parts, int nblocks, int nq, double* out) {
+  __shared__ double red[32];
+  for (int q = 0; q < nq; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += parts[(int64_t)b * nq + q];
+    const double tot = block_sum(s, red);
+    if (threadIdx.x == 0) out[q] = tot;
+    __syncthreads();
+  }
+}
+
+// ---- second-order log-det difference: Q = dA W with dA = At - A, row by row
+//      (dA is nonzero only on the free set, so each row is a short combination of W's rows)
+constexpr int QT = 256;
+constexpr int QCAP = 2048;
+__global__ void __launch_bounds__(QT) k_dA_times_W(const double* __restrict__ At,
+                                                   const double* __restrict__ A,
+                                                   const double* __restrict__ W, int64_t ld,
+                                                   int64_t n, double* __restrict__ Q) {
+  __shared__ int idx[QCAP];
+  __shared__ double val[QCAP];
+  __shared__ int cnt;
+  __shared__ int wcount[QT / 32];
+  const int64_t i = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t c = threadIdx.x; c < n; c += QT) Q[i * ld + c] = 0.0;
+  for (int64_t k0 = 0; k0 < n; k0 += QCAP) {
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    // compact the nonzeros of dA[i, k0 : k0 + QCAP) in index order
+    for (int64_t kb = k0; kb < min(n, k0 + (int64_t)QCAP); kb += QT) {
+      const int64_t k = kb + threadIdx.x;
+      double d = 0.0;
+      if (k < min(n, k0 + (int64_t)QCAP)) d = At[i * ld + k] - A[i * ld + k];
+      const unsigned m = __ballot_sync(0xffffffffu, d != 0.0);
+      if (lane == 0) wcount[warp] = __popc(m);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int base = cnt;
+        for (int w = 0; w < QT / 32; ++w) { const int c = wcount[w]; wcount[w] = base; base += c; }
+        cnt = base;
+      }
+      __syncthreads();
+      if (d != 0.0) {
+        const int pos = wcount[warp] + __popc(m & ((1u << lane) - 1u));
+        idx[pos] = (int)k;
+        val[pos] = d;
+      }
+      __syncthreads();
+    }
+    const int m = cnt;
+    if (m == 0) continue;
+    for (int64_t c = threadIdx.x; c < n; c += QT) {
+      double s = Q[i * ld + c];
+      for (int e = 0; e < m; ++e) s = fma(val[e], W[(int64_t)idx[e] * ld + c], s);
+      Q[i * ld + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- tr(Q) and tr(Q^2) = sum_ij Q_ij Q_ji over 32 x 32 tile pairs
+__global__ void __launch_bounds__(RT) k_trace_pairs(const double* __restrict__ Q, int64_t ld,
+                                                    int64_t n, int np, double* __restrict__ parts) {
+  __shared__ double a[32][33], b[32][33];
+  __shared__ double red[32];
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int bi, bj;
+    tri_tile(tt, bi, bj);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+      const int64_t i2 = (int64_t)bj * 32 + r, j2 = (int64_t)bi * 32 + tx;
+      a[r][tx] = (i < n && j < n) ? Q[i * ld + j] : 0.0;
+      b[r][tx] = (i2 < n && j2 < n) ? Q[i2 * ld + j2] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+      if (bi == bj) {
+        // Q_ij Q_ji over the whole diagonal tile, each unordered pair twice as in the sum
+        s2 += a[r][tx] * a[tx][r];
+        if (i == j) s1 += a[r][tx];
+      } else {
+        s2 += 2.0 * a[r][tx] * b[tx][r];
+      }
+    }
+  }
+  const double v0 = block_sum(s1, red);
+  const double v1 = block_sum(s2, red);
+  if (threadIdx.x == 0) {
+    parts[(int64_t)blockIdx.x * 2] = v0;
+    parts[(int64_t)blockIdx.x * 2 + 1] = v1;
+  }
+}
+
+// ---- padded (ld) -> dense (n) copy
+__global__ void k_unpad(const double* __restrict__ src, int64_t ld, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) dst[i * n + j] = src[i * ld + j];
+}
+__global__ void k_unpad_i8(const int8_t* __restrict__ src, int64_t ld, int64_t n, int8_t* __restrict__ dst) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) dst[i * n + j] = src[i * ld + j];
+}
+__global__ void k_pad_i8(const int8_t* __restrict__ src, int64_t n, int8_t* __restrict__ dst, int64_t ld) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) dst[i * ld + j] = src[i * n + j];
+}
+}  // namespace
+
+int red_blocks(int64_t work_rows) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, work_rows));
+}
+
+void load_symmetric(const void* src, bool f32, int64_t n, double* dst, int64_t ld, int np,
+                    double* vmax, int* bad, cudaStream_t st) {
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int grid = (int)std::min<int64_t>(ntiles, 4 * kRedBlocks);
+  if (f32)
+    k_load_sym<float><<<grid, dim3(32, 8), 0, st>>>((const float*)src, n, dst, ld, np, vmax, bad);
+  else
+    k_load_sym<double><<<grid, dim3(32, 8), 0, st>>>((const double*)src, n, dst, ld, np, vmax, bad);
+  LAUNCH_CHECK();
+}
+
+void init_diag(const double* S, int64_t ld, int64_t n, int np, double lam, double* A, cudaStream_t st) {
+  k_init_diag<<<(np + 255) / 256, 256, 0, st>>>(S, ld, n, np, lam, A);
+  LAUNCH_CHECK();
+}
+
+void pad_identity(double* A, int64_t ld, int64_t n, int np, cudaStream_t st) {
+  if (np > n) {
+    k_pad_identity<<<(int)((np - n + 255) / 256), 256, 0, st>>>(A, ld, n, np);
+    LAUNCH_CHECK();
+  }
+}
+
+void gradient(const double* S, const double* W, const double* A, int64_t ld, int64_t n, double lam,
+              double* X, int8_t* code, int64_t ldc, double* parts, double* out4, cudaStream_t st) {
+  const int g = red_blocks(n);
+  k_gradient<<<g, RT, 0, st>>>(S, W, A, ld, n, lam, X, code, ldc, parts);
+  LAUNCH_CHECK();
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 4, out4);
+  LAUNCH_CHECK();
+}
+
+void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, const double* S,
+           int64_t ld, int64_t n, int np, double lam, double t, double* At, double* Lt,
+           double* parts, double* out5, cudaStream_t st) {
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int g = (int)std::min<int64_t>(ntiles, kRedBlocks);
+  k_trial<<<g, RT, 0, st>>>(A, Y, code, ldc, S, ld, n, np, lam, t, At, Lt, parts);
+  LAUNCH_CHECK();
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 5, out5);
+  LAUNCH_CHECK();
+}
+
+void objective_terms(const double* S, const double* A, int64_t ld, int64_t n, double* parts,
+                     double* out2, cudaStream_t st) {
+  const int g = red_blocks(n);
+  k_objective_terms<<<g, RT, 0, st>>>(S, A, ld, n, parts);
+  LAUNCH_CHECK();
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 2, out2);
+  LAUNCH_CHECK();
+}
+
+void logdet_difference_terms(const double* At, const double* A, const double* W, int64_t ld,
+                             int64_t n, int np, double* Q, double* parts, double* out2,
+                             cudaStream_t st) {
+  k_dA_times_W<<<(int)n, QT, 0, st>>>(At, A, W, ld, n, Q);
+  LAUNCH_CHECK();
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int g = (int)std::min<int64_t>(ntiles, kRedBlocks);
+  k_trace_pairs<<<g, RT, 0, st>>>(Q, ld, n, np, parts);
+  LAUNCH_CHECK();
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 2, out2);
+  LAUNCH_CHECK();
+}
+
+void unpad(const double* src, int64_t ld, int64_t n, double* dst, cudaStream_t st) {
+  k_unpad<<<red_blocks(n), 256, 0, st>>>(src, ld, n, dst);
+  LAUNCH_CHECK();
+}
+void unpad_i8(const int8_t* src, int64_t ld, int64_t n, int8_t* dst, cudaStream_t st) {
+  k_unpad_i8<<<red_blocks(n), 256, 0, st>>>(src, ld, n, dst);
+  LAUNCH_CHECK();
+}
+void pad_i8(const int8_t* src, int64_t n, int8_t* dst, int64_t ld, cudaStream_t st) {
+  k_pad_i8<<<red_blocks(n), 256, 0, st>>>(src, n, dst, ld);
+  LAUNCH_CHECK();
+}
+
+}  // namespace glasso

@@ -1,0 +1,429 @@
+// pISTA outer loop (Algorithm 1) on the device kernels, with the line search of
+// Sec. 4.3.2 and the Sec. 6 fallback step, and the single-step operations of the C ABI.
+#include <cmath>
+#include <cstring>
+#include "engine.h"
+#include "gemm_tc.h"
+
+namespace glasso {
+
+namespace {
+constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
+constexpr double kDiffBand = 1000.0;                      // tier-2 band, in units of delta
+constexpr double kFallbackFactor = 0.9;                   // Sec. 6: t <= (0.9 / cond A)^2
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+// lower triangle of src (ld) -> dense dst (n), zero upper
+__global__ void k_unpad_lower(const double* __restrict__ src, int64_t ld, int64_t n, double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) dst[i * n + j] = (j <= i) ? src[i * ld + j] : 0.0;
+}
+
+// power iteration pieces: y = M x (one block per row), x = y / ||y||
+__global__ void k_gemv_rows(const double* __restrict__ M, int64_t ld, int64_t n, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  __shared__ double red[32];
+  const int64_t i = blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s = fma(M[i * ld + j], x[j], s);
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) y[i] = t;
+}
+__global__ void k_normalize(double* __restrict__ y, int64_t n, double* __restrict__ x, double* nrm) {
+  __shared__ double red[32];
+  __shared__ double tot;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s = fma(y[j], y[j], s);
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) { tot = sqrt(t); *nrm = tot; }
+  __syncthreads();
+  const double inv = tot > 0.0 ? 1.0 / tot : 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) x[j] = y[j] * inv;
+}
+__global__ void k_fill(double* x, int64_t n, double v) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = v;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// workspace
+// ------------------------------------------------------------------------------------------
+size_t Workspace::bytes_for(int np) {
+  const size_t m = (size_t)np * np;
+  return 9 * m * sizeof(double) + m + 2 * (size_t)np * kNb * sizeof(double) +
+         tc_scratch_bytes_for(np);
+}
+
+void Workspace::release() {
+  dfree(S); dfree(A); dfree(At); dfree(W); dfree(L); dfree(Lt); dfree(X); dfree(Y); dfree(T);
+  dfree(code); dfree(Dinv); dfree(Dinv_t); dfree(ld_parts); dfree(parts); dfree(sc);
+  dfree(pd); dfree(vmax); dfree(bad); dfree(vec);
+  if (staging) cudaFree(staging);
+  staging = nullptr;
+  staging_bytes = 0;
+  if (tc_scratch) cudaFree(tc_scratch);
+  tc_scratch = nullptr;
+  tc_scratch_bytes = 0;
+  if (hs) cudaFreeHost(hs);
+  hs = nullptr;
+  cap_np = 0;
+}
+
+void Workspace::ensure(int64_t n_new, size_t budget) {
+  const int np_new = (int)round_up(n_new, kPad);
+  if (np_new > cap_np) {
+    const size_t need = bytes_for(np_new);
+    if (budget && need > budget)
+      throw Error(GLASSO_ERR_BUDGET, "problem needs " + std::to_string(need) +
+                                         " bytes of device memory, budget is " +
+                                         std::to_string(budget));
+    release();
+    const size_t m = (size_t)np_new * np_new;
+    auto alloc = [&](auto*& p, size_t bytes) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        throw Error(GLASSO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+      }
+      p = reinterpret_cast<std::remove_reference_t<decltype(p)>>(q);
+    };
+    alloc(S, m * 8); alloc(A, m * 8); alloc(At, m * 8); alloc(W, m * 8); alloc(L, m * 8);
+    alloc(Lt, m * 8); alloc(X, m * 8); alloc(Y, m * 8); alloc(T, m * 8); alloc(code, m);
+    alloc(Dinv, (size_t)np_new * kNb * 8); alloc(Dinv_t, (size_t)np_new * kNb * 8);
+    alloc(ld_parts, (size_t)(np_new / kNb) * 8);
+    alloc(parts, (size_t)8 * kRedBlocks * 8);
+    alloc(sc, sizeof(Scalars));
+    alloc(pd, sizeof(int));
+    alloc(vmax, 2 * sizeof(double));
+    alloc(bad, sizeof(int));
+    alloc(vec, (size_t)3 * np_new * 8);
+    tc_scratch_bytes = tc_scratch_bytes_for(np_new);
+    if (tc_scratch_bytes) alloc(tc_scratch, tc_scratch_bytes);
+    if (cudaMallocHost((void**)&hs, sizeof(Scalars)) != cudaSuccess) {
+      cudaGetLastError();
+      hs = nullptr;
+      release();
+      throw Error(GLASSO_ERR_OOM, "cudaMallocHost failed");
+    }
+    cap_np = np_new;
+  }
+  n = n_new;
+  np = (int)round_up(n_new, kPad);
+  ld = np;
+}
+
+// ------------------------------------------------------------------------------------------
+// engine
+// ------------------------------------------------------------------------------------------
+Engine::Engine(const glasso_config& cfg) : cfg_(cfg) {
+  CUDA_CHECK(cudaSetDevice(cfg.device));
+  ws.device = cfg.device;
+  if (cfg.stream) {
+    stream_ = (cudaStream_t)cfg.stream;
+  } else {
+    CUDA_CHECK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+    own_stream_ = true;
+  }
+}
+
+Engine::~Engine() {
+  cudaSetDevice(cfg_.device);
+  if (stream_) cudaStreamSynchronize(stream_);
+  ws.release();
+  if (own_stream_ && stream_) cudaStreamDestroy(stream_);
+}
+
+void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
+  const bool mixed = cfg_.precision != GLASSO_FP64;
+  if (mixed && role != GemmRole::Panel && tc_gemm_supported(a)) {
+    tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
+            ws.tc_scratch, ws.tc_scratch_bytes, st);
+    return;
+  }
+  gemm_f64(a, 1, st);
+}
+
+GemmFn Engine::gemm_fn() {
+  return [this](const GemmArgs& a, GemmRole r, cudaStream_t st) { gemm(a, r, st); };
+}
+
+void Engine::sync_scalars() {
+  CUDA_CHECK(cudaMemcpyAsync(ws.hs, ws.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
+  CUDA_CHECK(cudaStreamSynchronize(stream_));
+}
+
+// Copy a caller matrix (n x n, leading dim n) into dst (padded), mirroring its lower
+// triangle; with check_s the S checks of glasso_solve are applied.
+void Engine::load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst,
+                         bool check_s) {
+  const size_t elt = f32 ? 4 : 8;
+  const size_t bytes = (size_t)n * n * elt;
+  const void* dsrc = src;
+  if (!on_device) {
+    if (ws.staging_bytes < bytes) {
+      if (ws.staging) cudaFree(ws.staging);
+      ws.staging = nullptr;
+      ws.staging_bytes = 0;
+      if (cudaMalloc(&ws.staging, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(GLASSO_ERR_OOM, "staging allocation failed");
+      }
+      ws.staging_bytes = bytes;
+    }
+    CUDA_CHECK(cudaMemcpyAsync(ws.staging, src, bytes, cudaMemcpyHostToDevice, stream_));
+    dsrc = ws.staging;
+  }
+  CUDA_CHECK(cudaMemsetAsync(ws.vmax, 0, 2 * sizeof(double), stream_));
+  CUDA_CHECK(cudaMemsetAsync(ws.bad, 0, sizeof(int), stream_));
+  load_symmetric(dsrc, f32, n, dst, ws.ld, ws.np, ws.vmax, ws.bad, stream_);
+  if (check_s) {
+    double vm[2];
+    int bad = 0;
+    CUDA_CHECK(cudaMemcpyAsync(vm, ws.vmax, sizeof(vm), cudaMemcpyDeviceToHost, stream_));
+    CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CUDA_CHECK(cudaStreamSynchronize(stream_));
+    if (bad) throw Error(GLASSO_ERR_NONFINITE, "S holds non-finite entries or a negative diagonal");
+    if (vm[0] > 1e-12 * vm[1])
+      throw Error(GLASSO_ERR_NOT_SYMMETRIC, "S is not symmetric: max |S_ij - S_ji| = " +
+                                                std::to_string(vm[0]));
+  }
+}
+
+void Engine::compute_inverse(const double* L, const double* Dinv, cudaStream_t st) {
+  inverse_from_factor(L, Dinv, ws.ld, ws.np, ws.X, ws.T, ws.W, gemm_fn(), st);
+  if (cfg_.precision != GLASSO_FP64) refine_inverse(*this, L, st);
+}
+
+// Y = lower(A X A): T = A X, then Y = T A on the lower triangle (Y is symmetric)
+void Engine::sandwich(cudaStream_t st) {
+  const int np = ws.np;
+  GemmArgs a = gemm_args(ws.A, ws.ld, 0, ws.X, ws.ld, 0, ws.T, ws.ld, np, np, np, 1.0, 0.0);
+  gemm(a, GemmRole::Sandwich, st);
+  GemmArgs b = gemm_args(ws.T, ws.ld, 0, ws.A, ws.ld, 0, ws.Y, ws.ld, np, np, np, 1.0, 0.0);
+  b.lower = 1;
+  gemm(b, GemmRole::Sandwich, st);
+}
+
+double Engine::power_lambda_max(const double* M, cudaStream_t st) {
+  const int64_t n = ws.n;
+  double* x = ws.vec;
+  double* y = ws.vec + ws.np;
+  double* nrm = ws.vec + 2 * ws.np;
+  k_fill<<<(int)((n + 255) / 256), 256, 0, st>>>(x, n, 1.0 / std::sqrt((double)n));
+  LAUNCH_CHECK();
+  for (int it = 0; it < 60; ++it) {
+    k_gemv_rows<<<(int)n, 256, 0, st>>>(M, ws.ld, n, x, y);
+    k_normalize<<<1, 1024, 0, st>>>(y, n, x, nrm);
+  }
+  LAUNCH_CHECK();
+  double h = 0.0;
+  CUDA_CHECK(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return h;
+}
+
+SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n, double lam,
+                       double tol, const double* theta0, double* theta_out, bool keep_trace) {
+  const auto t_begin = std::chrono::steady_clock::now();
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  const int np = ws.np;
+  const int64_t ld = ws.ld;
+  const size_t mat = sizeof(double) * ld * np;
+  Scalars& h = *ws.hs;
+  const double shrink = cfg_.shrink > 0 && cfg_.shrink < 1 ? cfg_.shrink : 0.5;
+  const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
+  const int max_iter = cfg_.max_iter > 0 ? cfg_.max_iter : 500;
+
+  load_matrix(Sin, s_f32, s_on_device, n, ws.S, true);
+  CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ld * np, st));
+  CUDA_CHECK(cudaMemsetAsync(ws.X, 0, mat, st));
+  if (theta0) {
+    load_matrix(theta0, false, s_on_device, n, ws.A, false);
+    pad_identity(ws.A, ld, n, np, st);
+  } else {
+    CUDA_CHECK(cudaMemsetAsync(ws.A, 0, mat, st));
+    init_diag(ws.S, ld, n, np, lam, ws.A, st);
+  }
+  // factor the start point
+  CUDA_CHECK(cudaMemcpyAsync(ws.Lt, ws.A, mat, cudaMemcpyDeviceToDevice, st));
+  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+  objective_terms(ws.S, ws.A, ld, n, ws.parts, &ws.sc->trsa, st);
+  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  sync_scalars();
+  if (!h.pd_t) throw Error(GLASSO_ERR_NOT_PD, "the start point is not positive definite");
+  std::swap(ws.L, ws.Lt);
+  std::swap(ws.Dinv, ws.Dinv_t);
+  double ld_A = h.logdet_t, trsa = h.trsa, l1 = h.l1;
+  double F = -ld_A + trsa + lam * l1;
+
+  SolveOut out;
+  int k = 0;
+  for (;;) {
+    compute_inverse(ws.L, ws.Dinv, st);
+    gradient(ws.S, ws.W, ws.A, ld, n, lam, ws.X, ws.code, ld, ws.parts, &ws.sc->z_l1, st);
+    sync_scalars();
+    out.r = h.z_l1 / h.a_l1;
+    out.z_fro = std::sqrt(h.z_fro2);
+    out.nnz = h.nnz;
+    if (out.r <= tol) { out.status = GLASSO_OK; break; }
+    if (k >= max_iter) { out.status = GLASSO_MAX_ITER; break; }
+    sandwich(st);
+    const double delta = 16.0 * kUnitRoundoff * (std::fabs(ld_A) + std::fabs(trsa) + lam * l1);
+    double t = 1.0, dF = INFINITY;
+    int trials = 0, tier = 1;
+    bool accepted = false;
+    auto try_step = [&](double tt) -> double {
+      trial(ws.A, ws.Y, ws.code, ld, ws.S, ld, n, np, lam, tt, ws.At, ws.Lt, ws.parts,
+            &ws.sc->lin_s, st);
+      k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+      cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+      CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+      sync_scalars();
+      ++trials;
+      tier = 1;
+      if (!h.pd_t) return INFINITY;
+      const double lin = h.lin_s + lam * h.lin_l1;
+      double d = -(h.logdet_t - ld_A) + lin;
+      if (std::fabs(d) <= kDiffBand * delta) {
+        // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3)
+        logdet_difference_terms(ws.At, ws.A, ws.W, ld, n, np, ws.T, ws.parts, &ws.sc->tr_e, st);
+        sync_scalars();
+        d = -(h.tr_e - 0.5 * h.tr_e2) + lin;
+        tier = 2;
+      }
+      return d;
+    };
+    while (t >= t_min) {
+      dF = try_step(t);
+      if (dF < 0.0) { accepted = true; break; }
+      t *= shrink;
+    }
+    if (!accepted) {
+      const double lmax_a = power_lambda_max(ws.A, st);
+      const double lmax_w = power_lambda_max(ws.W, st);
+      t = std::pow(kFallbackFactor / (lmax_a * lmax_w), 2.0);
+      dF = try_step(t);
+      accepted = dF < 0.0;
+    }
+    out.trials += trials;
+    if (keep_trace)
+      out.trace.push_back(IterRecord{k, trials, tier, F, out.r, out.z_fro, out.nnz, t, dF});
+    if (!accepted) { out.status = GLASSO_LINESEARCH_STALL; break; }
+    std::swap(ws.A, ws.At);
+    std::swap(ws.L, ws.Lt);
+    std::swap(ws.Dinv, ws.Dinv_t);
+    ld_A = h.logdet_t;
+    trsa = h.trsa_t;
+    l1 = h.l1_t;
+    F = -ld_A + trsa + lam * l1;
+    ++k;
+  }
+  out.iterations = k;
+  out.F = F;
+  out.logdet = ld_A;
+  if (theta_out) {
+    if (s_on_device) {
+      unpad(ws.A, ld, n, theta_out, st);
+    } else {
+      unpad(ws.A, ld, n, ws.T, st);
+      CUDA_CHECK(cudaMemcpyAsync(theta_out, ws.T, sizeof(double) * n * n, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_begin).count();
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------
+// single steps
+// ------------------------------------------------------------------------------------------
+void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet) {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  load_matrix(A, false, true, n, ws.Lt, false);
+  pad_identity(ws.Lt, ws.ld, n, ws.np, st);
+  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  cholesky_f64(ws.Lt, ws.ld, ws.np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  k_unpad_lower<<<red_blocks(n), 256, 0, st>>>(ws.Lt, ws.ld, n, L);
+  LAUNCH_CHECK();
+  sync_scalars();
+  *pd = ws.hs->pd_t;
+  *logdet = ws.hs->logdet_t;
+}
+
+int Engine::op_inverse(const double* A, int64_t n, double* W) {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  load_matrix(A, false, true, n, ws.A, false);
+  pad_identity(ws.A, ws.ld, n, ws.np, st);
+  CUDA_CHECK(cudaMemcpyAsync(ws.L, ws.A, sizeof(double) * ws.ld * ws.np, cudaMemcpyDeviceToDevice, st));
+  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  cholesky_f64(ws.L, ws.ld, ws.np, ws.Dinv, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  sync_scalars();
+  if (!ws.hs->pd_t) return 0;
+  compute_inverse(ws.L, ws.Dinv, st);
+  unpad(ws.W, ws.ld, n, W, st);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return 1;
+}
+
+void Engine::op_gradient(const double* S, const double* A, const double* W, int64_t n, double lam,
+                         double* X, int8_t* code, double sums[4]) {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  load_matrix(S, false, true, n, ws.S, false);
+  load_matrix(A, false, true, n, ws.A, false);
+  load_matrix(W, false, true, n, ws.W, false);
+  gradient(ws.S, ws.W, ws.A, ws.ld, n, lam, ws.X, ws.code, ws.ld, ws.parts, &ws.sc->z_l1, st);
+  unpad(ws.X, ws.ld, n, X, st);
+  unpad_i8(ws.code, ws.ld, n, code, st);
+  sync_scalars();
+  sums[0] = ws.hs->z_l1; sums[1] = ws.hs->a_l1; sums[2] = ws.hs->z_fro2; sums[3] = ws.hs->nnz;
+}
+
+void Engine::op_sandwich(const double* A, const double* X, int64_t n, double* Y) {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  load_matrix(A, false, true, n, ws.A, false);
+  load_matrix(X, false, true, n, ws.X, false);
+  sandwich(st);
+  mirror_lower(ws.Y, ws.ld, ws.np, st);
+  unpad(ws.Y, ws.ld, n, Y, st);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+void Engine::op_trial(const double* A, const double* Y, const int8_t* code, int64_t n, double lam,
+                      double t, double* At) {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  cudaStream_t st = stream_;
+  load_matrix(A, false, true, n, ws.A, false);
+  load_matrix(Y, false, true, n, ws.Y, false);
+  CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ws.ld * ws.np, st));
+  pad_i8(code, n, ws.code, ws.ld, st);
+  CUDA_CHECK(cudaMemsetAsync(ws.S, 0, sizeof(double) * ws.ld * ws.np, st));
+  trial(ws.A, ws.Y, ws.code, ws.ld, ws.S, ws.ld, n, ws.np, lam, t, ws.At, ws.Lt, ws.parts,
+        &ws.sc->lin_s, st);
+  unpad(ws.At, ws.ld, n, At, st);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+}  // namespace glasso

@@ -1,0 +1,92 @@
+// Host-side solver engine behind the C ABI: device workspaces, the pISTA outer loop with
+// its line search (Algorithm 1), and the GEMM dispatch by precision mode.
+#pragma once
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <vector>
+#include "../../include/glasso.h"
+#include "elementwise.h"
+#include "factor.h"
+
+namespace glasso {
+
+// Device buffers of one problem of padded size np (all np x np FP64 unless noted).
+struct Workspace {
+  int device = 0;
+  int64_t n = 0, ld = 0;
+  int np = 0, cap_np = 0;
+  double *S = nullptr, *A = nullptr, *At = nullptr, *W = nullptr, *L = nullptr, *Lt = nullptr;
+  double *X = nullptr, *Y = nullptr, *T = nullptr;
+  int8_t* code = nullptr;                 // np x np
+  double *Dinv = nullptr, *Dinv_t = nullptr;  // np x 64 each
+  double* ld_parts = nullptr;             // np / 64
+  double* parts = nullptr;                // 8 * kRedBlocks
+  Scalars* sc = nullptr;                  // device scalars
+  Scalars* hs = nullptr;                  // pinned host mirror
+  int* pd = nullptr;                      // device PD flag
+  double* vmax = nullptr;                 // [2]
+  int* bad = nullptr;
+  double* vec = nullptr;                  // 2 * np (power iteration)
+  void* staging = nullptr;                // caller-sized staging for host inputs
+  size_t staging_bytes = 0;
+  void* tc_scratch = nullptr;             // split operands of the tensor-core GEMMs
+  size_t tc_scratch_bytes = 0;
+
+  static size_t bytes_for(int np);
+  void ensure(int64_t n_new, size_t budget);  // (re)allocate for n_new; throws on failure
+  void release();
+  ~Workspace() { release(); }
+};
+
+struct IterRecord {
+  int k, trials, tier;
+  double F, r, z_fro, nnz, t, dF;
+};
+
+struct SolveOut {
+  int status = 0;
+  int iterations = 0, trials = 0;
+  double r = 0, z_fro = 0, F = 0, logdet = 0, nnz = 0, seconds = 0;
+  std::vector<IterRecord> trace;
+};
+
+class Engine {
+ public:
+  explicit Engine(const glasso_config& cfg);
+  ~Engine();
+  const glasso_config& config() const { return cfg_; }
+  cudaStream_t stream() const { return stream_; }
+
+  // Full pISTA solve.  S is the caller's n x n matrix (host or device); theta0 may be null.
+  SolveOut solve(const void* S, bool s_f32, bool s_on_device, int64_t n, double lam, double tol,
+                 const double* theta0, double* theta_out, bool keep_trace = false);
+
+  // single steps on caller device arrays (leading dimension n)
+  void op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet);
+  int op_inverse(const double* A, int64_t n, double* W);
+  void op_gradient(const double* S, const double* A, const double* W, int64_t n, double lam,
+                   double* X, int8_t* code, double sums[4]);
+  void op_sandwich(const double* A, const double* X, int64_t n, double* Y);
+  void op_trial(const double* A, const double* Y, const int8_t* code, int64_t n, double lam,
+                double t, double* At);
+
+  // the GEMM used for a given role in the configured precision mode
+  void gemm(const GemmArgs& a, GemmRole role, cudaStream_t st);
+  GemmFn gemm_fn();
+
+  Workspace ws;
+
+ private:
+  void load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst, bool check_s);
+  void sandwich(cudaStream_t st);
+  void compute_inverse(const double* L, const double* Dinv, cudaStream_t st);
+  double power_lambda_max(const double* M, cudaStream_t st);
+  void sync_scalars();
+
+  glasso_config cfg_;
+  cudaStream_t stream_ = nullptr;
+  bool own_stream_ = false;
+};
+
+}  // namespace glasso

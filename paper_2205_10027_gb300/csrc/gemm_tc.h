@@ -1,0 +1,21 @@
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+#pragma once
+#include "gemm.h"
+
+namespace glasso {
+
+class Engine;
+
+enum class TcKind { TF32x3, BF16x3 };
+
+// Device scratch the split operands of an np x np product need.
+size_t tc_scratch_bytes_for(int np);
+// Whether the tensor-core kernel covers this product's shape and options.
+bool tc_gemm_supported(const GemmArgs& a);
+// C = alpha op(A) op(B) + beta C with each FP64 operand split into hi + lo parts and the
+// three products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, then added to C in FP64.
+void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st);
+// Mixed mode: one Newton-Schulz sweep W <- W + W (I - A W) with the residual in FP64.
+void refine_inverse(Engine& e, const double* L, cudaStream_t st);
+
+}  // namespace glasso

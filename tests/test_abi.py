@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every entry point include/glasso.h declares; its
+argument checks answer without touching a GPU.  CPU only."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "glasso.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(glasso_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("glasso_create", "glasso_destroy", "glasso_solve", "glasso_solve_batch",
+                     "glasso_submit", "glasso_poll", "glasso_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(glasso):
+    lib = C.CDLL(glasso.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared()) == set(glasso.EXPORTED)
+
+
+def test_status_strings_and_defaults(glasso):
+    assert glasso.glasso_status_string(0) == b"GLASSO_OK"
+    assert glasso.glasso_status_string(10) == b"GLASSO_LINESEARCH_STALL"
+    cfg = glasso.glasso_config()
+    assert glasso.glasso_config_default(C.byref(cfg)) == 0
+    assert cfg.max_iter == 500 and cfg.shrink == 0.5 and cfg.t_min == 1e-4 and cfg.precision == 0
+
+
+def test_argument_checks_need_no_gpu(glasso):
+    # NULL handle / NULL outputs are rejected before any CUDA call
+    assert glasso.glasso_create(None, None) == 1
+    assert glasso.glasso_solve(None, None, 0, 0, 10, 0.1, 1e-6, None, None, None) == 1
+    assert glasso.glasso_destroy(None) == 0
+    assert glasso.glasso_last_error(None) == b""
+
+
+def test_create_without_a_gpu_is_refused_cleanly(glasso):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = glasso.glasso_config()
+    glasso.glasso_config_default(C.byref(cfg))
+    h = C.c_void_p()
+    assert glasso.glasso_create(C.byref(cfg), C.byref(h)) == 12  # GLASSO_ERR_UNSUPPORTED
+    assert not h.value
