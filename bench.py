@@ -1,0 +1,305 @@
+"""Benchmark: pISTA outer iterations per second on the n = 10,000 grid workload.
+
+One step is one outer iteration of Algorithm 1 through the library (W = Theta^{-1} from the
+cached factor, gradient / free set / sign guess / stop test, the sandwich products of eq. b,
+and the line search with a Cholesky factorisation per trial), on a 100 x 100 lattice
+precision (4-neighbour weights -1, diagonal 4.1), m = 2,000 samples, lambda = 0.1.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3|bf16x3]
+  python bench.py --impl reference ...   the FP64 CPU oracle on a bounded sample
+
+For N > 1 (torchrun) every rank solves its own replica (the single solve does not shard):
+value = the iterations of all ranks / the slowest rank's time.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pISTA iters/s (n=10k grid, lambda=0.1); time-to-KKT 1e-6"
+UNIT = "iters/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        smax = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def workload(side: int, m: int):
+    from paper_2205_10027_gb300 import inputs
+    return inputs.grid_n10000(side=side, m=m, seed=2, lam=0.1)
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle legs
+# ----------------------------------------------------------------------------------------
+def oracle_rate(sample_side: int, full_n: int, iters: int):
+    """Oracle iterations/s on a bounded sample (a smaller lattice of the same family),
+    scaled to the full size by the n^3 work of an iteration."""
+    from oracle import pista
+    p = workload(sample_side, max(2, sample_side * sample_side // 5))
+    t0 = time.perf_counter()
+    res = pista.pista(p.S, p.lam, tol=0.0, max_iter=iters)
+    dt = time.perf_counter() - t0
+    ns = sample_side * sample_side
+    rate = res["iterations"] / dt * (ns / full_n) ** 3
+    return rate, dt, res["iterations"], ns
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    full_n = args.side * args.side
+    cores = os.cpu_count()
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(args.sample_side, full_n, 1)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, _, ns = oracle_rate(args.sample_side, full_n, 1)
+        rates.append(r)
+    elapsed = time.perf_counter() - t_all
+    value = statistics.median(rates)
+    sample = (f"one oracle iteration per step on a {args.sample_side}x{args.sample_side} lattice "
+              f"(n={args.sample_side ** 2}, m=n/5) from the start point, scaled by (n_sample/n)^3")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"grid{args.side}x{args.side}_n{full_n}_m{args.m}_lam0.1",
+                                        "sample_n": args.sample_side ** 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2205_10027_gb300 import binding
+
+    p = workload(args.side, args.m)
+    n = p.S.shape[0]
+    S_dev = torch.from_numpy(np.ascontiguousarray(p.S)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    h = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident steps -------------------------------------------------------------
+    h.begin(S_dev, p.lam)
+    for _ in range(args.warmup):
+        h.step(0.0)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    trials = 0
+    with ClockSampler(local) as clk:
+        h.profile_start()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, res = h.step(0.0)
+            launches += res["kernel_launches"]
+            trials += res["trials"]
+        e1.record(stream)
+        barrier()
+        prof = h.profile_stop()
+    ms = e0.elapsed_time(e1)
+    last = res
+    h.end()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # ---- end to end through the public API, host buffers ------------------------------------
+    S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
+    out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    he = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
+                        max_iter=args.steps)
+    he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())  # warm the workspace
+    barrier()
+    t0 = time.perf_counter()
+    _, res_e2e = he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    he.close()
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * res_e2e["iterations"] / e2e_s
+
+    # ---- time to tolerance (device-resident) ---------------------------------------------------
+    ttt = None
+    if args.time_to_tol:
+        ht = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream, max_iter=2000)
+        barrier()
+        t0 = time.perf_counter()
+        _, rt = ht.solve(S_dev, p.lam, p.tol)
+        barrier()
+        ttt = {"seconds": time.perf_counter() - t0, "iterations": rt["iterations"], "trials": rt["trials"],
+               "rel_kkt_l1": rt["rel_kkt_l1"], "status": binding.STATUS[rt["status"]]}
+        ht.close()
+    h.close()
+
+    if rank == 0:
+        peaks, peak_kind = _peaks()
+        # dominant kernel: the dense-product kernel (all GEMM classes are launches of it)
+        gemm_cls = [c for c in ("sandwich", "trailing", "panel", "inverse", "refine") if c in prof]
+        g_ms = sum(prof[c]["ms"] for c in gemm_cls)
+        g_work = sum(prof[c]["work"] for c in gemm_cls)
+        g_launch = sum(prof[c]["launches"] for c in gemm_cls)
+        achieved = g_work / (g_ms / 1000.0) / 1e12 if g_ms else 0.0
+        if args.precision == "fp64":
+            # FP64 runs on the CUDA cores' FP64 pipe: peak measured live by an FMA-chain kernel
+            peak = binding.probe_fp64_peak(local)
+            peak_kind = "measured live (FP64 FMA-chain kernel in libglasso)"
+            bound, kernel = "alu", "k_gemm_f64"
+        else:
+            ratio = (1100.0 / 2250.0) if args.precision == "tf32x3" else 1.0
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * ratio / 3.0
+            bound, kernel = "tensor", "k_gemm_tc"
+        rl = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+              "frac": achieved / peak if peak else None, "traffic": None,
+              "peak_source": peak_kind if args.precision == "fp64" else f"{peak_kind} bf16 sustained x nominal dtype ratio / 3 split products",
+              "launches": g_launch, "share_of_step": g_ms / ms if ms else None}
+        hbm = {}
+        for c in ("gradient", "trial"):
+            if c in prof and prof[c]["ms"]:
+                gbs = prof[c]["work"] / (prof[c]["ms"] / 1000.0) / 1e9
+                hbm[c] = {"achieved_gbs": gbs, "frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                          "launches": prof[c]["launches"], "ms": prof[c]["ms"]}
+        cpu = None
+        if not args.no_cpu_baseline:
+            rate, dt, its, ns = oracle_rate(args.sample_side, n, 2)
+            cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{its} oracle iterations on a {args.sample_side}x{args.sample_side} lattice "
+                             f"(n={ns}, m=n/5) in {dt:.1f}s, scaled to n={n} by (n_sample/n)^3"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "tf32x3": "f64+tf32x3", "bf16x3": "f64+bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"grid{args.side}x{args.side}_n{n}_m{args.m}_lam0.1",
+                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (each n x n FP64 matrix is %.0f MB)" % (8 * n * n / 1e6)},
+            "gpu_launches": launches, "trials_in_timed_steps": trials,
+            "last_step": {"rel_kkt_l1": last["rel_kkt_l1"], "iterations": last["iterations"]},
+            "roofline": rl, "hbm_passes": hbm, "profile": prof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n / max(res_e2e["iterations"], 1),
+                    "d2h_bytes_per_step": 8 * n * n / max(res_e2e["iterations"], 1),
+                    "note": "one glasso_solve from pinned host S to host Theta, max_iter=steps"},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "time_to_tol": ttt,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="fp64")
+    ap.add_argument("--side", type=int, default=100)
+    ap.add_argument("--m", type=int, default=2000)
+    ap.add_argument("--sample-side", type=int, default=50)
+    ap.add_argument("--time-to-tol", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

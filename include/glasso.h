@@ -81,6 +81,7 @@ typedef struct {
   double logdet;            /* log det Theta */
   double seconds;           /* wall time of the solve inside the library */
   double t_submit, t_start, t_done;  /* serving timestamps (s, monotonic clock), else 0 */
+  int64_t kernel_launches;  /* CUDA kernels this solve (or step) launched */
 } glasso_result;
 
 /* ---- handle ------------------------------------------------------------------------------ */
@@ -117,6 +118,52 @@ const char* glasso_status_string(glasso_status s);
 glasso_status glasso_solve(glasso_handle* h, const void* S, glasso_dtype s_dtype,
                            glasso_memory where, int64_t n, double lambda, double tol,
                            const double* theta0, double* theta_out, glasso_result* res);
+
+/* ---- step-wise solve: the same iteration as glasso_solve, one outer iteration per call ---- */
+
+/* Load S and the start point as glasso_solve does and factor the start point.  The handle
+ * then holds the iterate until glasso_end (or the next glasso_begin / glasso_solve). */
+glasso_status glasso_begin(glasso_handle* h, const void* S, glasso_dtype s_dtype,
+                           glasso_memory where, int64_t n, double lambda, const double* theta0);
+
+/* One outer iteration of Algorithm 1: W = Theta^{-1}, gradient and stop test; if
+ * ||Z||_1 > tol ||Theta||_1, the direction and the line search.  Returns GLASSO_PENDING
+ * when a step was accepted, GLASSO_OK when the stop test held (no step taken),
+ * GLASSO_LINESEARCH_STALL when no trial passed.  res (optional) describes the iterate the
+ * stop test saw and counts this call's trials and kernel launches. */
+glasso_status glasso_step(glasso_handle* h, double tol, glasso_result* res);
+
+/* Copy the current iterate to theta_out (n x n FP64, the memory kind given to
+ * glasso_begin; may be NULL) and end the step-wise solve. */
+glasso_status glasso_end(glasso_handle* h, double* theta_out, glasso_result* res);
+
+/* ---- device-time accounting of the kernel classes (CUDA events around each launch) --------- */
+
+enum {
+  GLASSO_PROF_SANDWICH = 0,   /* the two products of eq. b: FLOPs */
+  GLASSO_PROF_TRAILING = 1,   /* Cholesky trailing updates: FLOPs */
+  GLASSO_PROF_PANEL = 2,      /* Cholesky panel solves: FLOPs */
+  GLASSO_PROF_INVERSE = 3,    /* triangular inverse and W = X^T X: FLOPs */
+  GLASSO_PROF_REFINE = 4,     /* mixed mode: refinement products of W: FLOPs */
+  GLASSO_PROF_GRADIENT = 5,   /* gradient / free-set / KKT pass: bytes moved */
+  GLASSO_PROF_TRIAL = 6,      /* trial-point pass: bytes moved */
+  GLASSO_PROF_CLASSES = 8
+};
+
+typedef struct {
+  double ms[GLASSO_PROF_CLASSES];      /* summed device time of the class's launches */
+  double work[GLASSO_PROF_CLASSES];    /* algorithmic FLOPs or bytes of those launches */
+  int64_t launches[GLASSO_PROF_CLASSES];
+} glasso_profile;
+
+/* Start recording (clears earlier records).  Adds two event records per launch. */
+glasso_status glasso_profile_start(glasso_handle* h);
+/* Wait for the recorded work, fill *out and stop recording. */
+glasso_status glasso_profile_stop(glasso_handle* h, glasso_profile* out);
+
+/* Peak FP64 FMA throughput of a device in TFLOP/s, measured by a register-resident FMA
+ * kernel (the roofline denominator of the FP64 form; it allocates a small buffer). */
+glasso_status glasso_probe_fp64_peak(int device, double* tflops);
 
 /* ---- batched regularisation paths -------------------------------------------------------- */
 

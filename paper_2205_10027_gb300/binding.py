@@ -39,10 +39,22 @@ class glasso_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("trials", C.c_int32),
                 ("nnz", C.c_int32), ("rel_kkt_l1", C.c_double), ("min_subgrad_fro", C.c_double),
                 ("objective", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
-                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PROF_CLASSES = ("sandwich", "trailing", "panel", "inverse", "refine", "gradient", "trial", "unused")
+
+
+class glasso_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("work", C.c_double * 8), ("launches", C.c_int64 * 8)]
+
+    def as_dict(self):
+        return {name: dict(ms=self.ms[i], work=self.work[i], launches=self.launches[i])
+                for i, name in enumerate(PROF_CLASSES) if self.launches[i]}
 
 
 class glasso_problem(C.Structure):
@@ -66,6 +78,12 @@ _sig = {
     "glasso_status_string": (C.c_char_p, [C.c_int]),
     "glasso_solve": (C.c_int, [_h, _dp, C.c_int, C.c_int, C.c_int64, C.c_double, C.c_double, _dp, _dp,
                                C.POINTER(glasso_result)]),
+    "glasso_begin": (C.c_int, [_h, _dp, C.c_int, C.c_int, C.c_int64, C.c_double, _dp]),
+    "glasso_step": (C.c_int, [_h, C.c_double, C.POINTER(glasso_result)]),
+    "glasso_end": (C.c_int, [_h, _dp, C.POINTER(glasso_result)]),
+    "glasso_profile_start": (C.c_int, [_h]),
+    "glasso_profile_stop": (C.c_int, [_h, C.POINTER(glasso_profile)]),
+    "glasso_probe_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "glasso_solve_batch": (C.c_int, [_h, C.POINTER(glasso_problem), C.c_int32, C.POINTER(glasso_result)]),
     "glasso_submit": (C.c_int, [_h, C.POINTER(glasso_request), C.POINTER(C.c_uint64)]),
     "glasso_poll": (C.c_int, [_h, C.c_uint64, C.POINTER(glasso_result), _dp]),
@@ -97,6 +115,15 @@ def _ptr(x):
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     return x.data_ptr()
+
+
+def probe_fp64_peak(device=0):
+    """Measured FP64 FMA peak of the device, TFLOP/s."""
+    v = C.c_double()
+    st = glasso_probe_fp64_peak(device, C.byref(v))
+    if st != OK:
+        raise GlassoError(st, "glasso_probe_fp64_peak failed")
+    return v.value
 
 
 class Handle:
@@ -165,6 +192,39 @@ class Handle:
                               tol, _ptr(theta0), _ptr(out), C.byref(res))
         self._check(st, allow)
         return out, res.as_dict()
+
+    # ---- step-wise solve -------------------------------------------------------------------
+    def begin(self, S, lam, theta0=None):
+        if isinstance(S, np.ndarray):
+            S = np.ascontiguousarray(S)
+            self._keep = S
+            st = glasso_begin(self.h, _ptr(S), F32 if S.dtype == np.float32 else F64, HOST, S.shape[0], lam,
+                              _ptr(None if theta0 is None else np.ascontiguousarray(theta0, np.float64)))
+        else:
+            import torch
+            st = glasso_begin(self.h, _ptr(S), F32 if S.dtype == torch.float32 else F64, DEVICE, S.shape[0],
+                              lam, _ptr(theta0))
+        self._check(st)
+
+    def step(self, tol=0.0):
+        """One outer iteration; returns (status, result dict).  status PENDING = step taken."""
+        res = glasso_result()
+        st = glasso_step(self.h, tol, C.byref(res))
+        self._check(st, (OK, PENDING, STALL))
+        return st, res.as_dict()
+
+    def end(self, out=None):
+        res = glasso_result()
+        self._check(glasso_end(self.h, _ptr(out), C.byref(res)))
+        return out, res.as_dict()
+
+    def profile_start(self):
+        self._check(glasso_profile_start(self.h))
+
+    def profile_stop(self):
+        p = glasso_profile()
+        self._check(glasso_profile_stop(self.h, C.byref(p)))
+        return p.as_dict()
 
     def solve_batch(self, problems):
         """problems: list of dict(S=np.ndarray (f32/f64), lambdas=[...], tol=...).

@@ -46,6 +46,7 @@ void fill_result(glasso_result* res, const glasso::SolveOut& o) {
   res->objective = o.F;
   res->logdet = o.logdet;
   res->seconds = o.seconds;
+  res->kernel_launches = o.launches;
 }
 
 bool valid_problem(int64_t n, double lambda, double tol) {
@@ -144,6 +145,81 @@ glasso_status glasso_solve(glasso_handle* h, const void* S, glasso_dtype s_dtype
                                           lambda, tol, theta0, theta_out);
     fill_result(res, o);
     return (glasso_status)o.status;
+  });
+}
+
+glasso_status glasso_begin(glasso_handle* h, const void* S, glasso_dtype s_dtype,
+                           glasso_memory where, int64_t n, double lambda, const double* theta0) {
+  if (!h || !S) return GLASSO_ERR_ARG;
+  if (!valid_problem(n, lambda, 0.0) || (s_dtype != GLASSO_F64 && s_dtype != GLASSO_F32) ||
+      (where != GLASSO_HOST && where != GLASSO_DEVICE))
+    return fail(h, GLASSO_ERR_ARG, "invalid n, lambda, dtype or memory kind");
+  std::lock_guard<std::mutex> lock(h->mu);
+  return guarded(h, [&] {
+    h->engine->begin(S, s_dtype == GLASSO_F32, where == GLASSO_DEVICE, n, lambda, theta0);
+    return GLASSO_OK;
+  });
+}
+
+glasso_status glasso_step(glasso_handle* h, double tol, glasso_result* res) {
+  if (!h || !(tol >= 0.0)) return GLASSO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return guarded(h, [&] {
+    const int64_t l0 = glasso::thread_launches();
+    const int t0 = h->engine->state().out.trials;
+    const int st = h->engine->step(tol, INT32_MAX, false);
+    if (res) {
+      const glasso::SolveState& s = h->engine->state();
+      glasso::SolveOut o;
+      o.status = st < 0 ? GLASSO_PENDING : st;
+      o.iterations = s.k;
+      o.trials = s.out.trials - t0;
+      o.r = s.out.r;
+      o.z_fro = s.out.z_fro;
+      o.nnz = s.out.nnz;
+      o.F = s.F;
+      o.logdet = s.ld_A;
+      o.launches = glasso::thread_launches() - l0;
+      fill_result(res, o);
+    }
+    return st < 0 ? GLASSO_PENDING : (glasso_status)st;
+  });
+}
+
+glasso_status glasso_end(glasso_handle* h, double* theta_out, glasso_result* res) {
+  if (!h) return GLASSO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return guarded(h, [&] {
+    glasso::SolveOut o = h->engine->finish(theta_out);
+    o.status = GLASSO_OK;
+    fill_result(res, o);
+    return GLASSO_OK;
+  });
+}
+
+glasso_status glasso_profile_start(glasso_handle* h) {
+  if (!h) return GLASSO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return guarded(h, [&] {
+    h->engine->prof.start();
+    return GLASSO_OK;
+  });
+}
+
+glasso_status glasso_profile_stop(glasso_handle* h, glasso_profile* out) {
+  if (!h || !out) return GLASSO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return guarded(h, [&] {
+    h->engine->prof.collect(out);
+    return GLASSO_OK;
+  });
+}
+
+glasso_status glasso_probe_fp64_peak(int device, double* tflops) {
+  if (!tflops) return GLASSO_ERR_ARG;
+  return guarded(nullptr, [&] {
+    *tflops = glasso::probe_fp64_tflops(device);
+    return GLASSO_OK;
   });
 }
 

@@ -83,4 +83,12 @@ struct Error : std::runtime_error {
       throw ::glasso::Error(7, std::string(#expr) + ": " + cudaGetErrorString(_e) +      \
                                    " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
   } while (0)
-#define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
+namespace glasso {
+// per-thread count of kernel launches (incremented at every checked launch)
+extern thread_local int64_t tl_launches;
+}
+#define LAUNCH_CHECK()                    \
+  do {                                    \
+    ++::glasso::tl_launches;              \
+    CUDA_CHECK(cudaGetLastError());       \
+  } while (0)

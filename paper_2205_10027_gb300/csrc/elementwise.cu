@@ -241,25 +241,30 @@ __global__ void k_finalize(const double* __restrict__ parts, int nblocks, int nq
 //      (dA is nonzero only on the free set, so each row is a short combination of W's rows)
 constexpr int QT = 256;
 constexpr int QCAP = 2048;
-__global__ void __launch_bounds__(QT) k_dA_times_W(const double* __restrict__ At,
-                                                   const double* __restrict__ A,
-                                                   const double* __restrict__ W, int64_t ld,
-                                                   int64_t n, double* __restrict__ Q) {
+__global__ void __launch_bounds__(QT) k_rows_times_W(const double* __restrict__ P,
+                                                     const double* __restrict__ Pm,
+                                                     const double* __restrict__ W, int64_t ld,
+                                                     int64_t n, int np, double sign, int identity,
+                                                     double* __restrict__ Q, double* rmax) {
   __shared__ int idx[QCAP];
   __shared__ double val[QCAP];
   __shared__ int cnt;
   __shared__ int wcount[QT / 32];
   const int64_t i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t c = threadIdx.x; c < n; c += QT) Q[i * ld + c] = 0.0;
+  if (i >= n) {  // padding rows of Q are zero
+    for (int64_t c = threadIdx.x; c < np; c += QT) Q[i * ld + c] = 0.0;
+    return;
+  }
+  for (int64_t c = threadIdx.x; c < np; c += QT) Q[i * ld + c] = (identity && c == i) ? 1.0 : 0.0;
   for (int64_t k0 = 0; k0 < n; k0 += QCAP) {
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    // compact the nonzeros of dA[i, k0 : k0 + QCAP) in index order
+    // compact the nonzeros of D[i, k0 : k0 + QCAP), D = P - Pm, in index order
     for (int64_t kb = k0; kb < min(n, k0 + (int64_t)QCAP); kb += QT) {
       const int64_t k = kb + threadIdx.x;
       double d = 0.0;
-      if (k < min(n, k0 + (int64_t)QCAP)) d = At[i * ld + k] - A[i * ld + k];
+      if (k < min(n, k0 + (int64_t)QCAP)) d = Pm ? P[i * ld + k] - Pm[i * ld + k] : P[i * ld + k];
       const unsigned m = __ballot_sync(0xffffffffu, d != 0.0);
       if (lane == 0) wcount[warp] = __popc(m);
       __syncthreads();
@@ -277,13 +282,41 @@ __global__ void __launch_bounds__(QT) k_dA_times_W(const double* __restrict__ At
       __syncthreads();
     }
     const int m = cnt;
-    if (m == 0) continue;
-    for (int64_t c = threadIdx.x; c < n; c += QT) {
-      double s = Q[i * ld + c];
-      for (int e = 0; e < m; ++e) s = fma(val[e], W[(int64_t)idx[e] * ld + c], s);
-      Q[i * ld + c] = s;
+    if (m > 0) {
+      for (int64_t c = threadIdx.x; c < n; c += QT) {
+        double s = 0.0;
+        for (int e = 0; e < m; ++e) s = fma(val[e], W[(int64_t)idx[e] * ld + c], s);
+        Q[i * ld + c] += sign * s;
+      }
     }
     __syncthreads();
+  }
+  if (rmax) {
+    double mx = 0.0;
+    for (int64_t c = threadIdx.x; c < n; c += QT) mx = fmax(mx, fabs(Q[i * ld + c]));
+    if (mx > 0.0) atomic_max_nonneg(rmax, mx);
+  }
+}
+
+// ---- W (lower) += C (lower), then the upper triangle of W := transpose of the lower
+__global__ void k_add_lower_mirror(double* __restrict__ W, const double* __restrict__ C, int64_t ld, int np) {
+  __shared__ double t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi < bj) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+    double v = W[i * ld + j];
+    if (j <= i) {
+      v += C[i * ld + j];
+      W[i * ld + j] = v;
+    }
+    t[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = (int64_t)bj * 32 + r, j = (int64_t)bi * 32 + tx;  // destination (upper)
+    if (j > i) W[i * ld + j] = t[tx][r];
   }
 }
 
@@ -402,7 +435,7 @@ void objective_terms(const double* S, const double* A, int64_t ld, int64_t n, do
 void logdet_difference_terms(const double* At, const double* A, const double* W, int64_t ld,
                              int64_t n, int np, double* Q, double* parts, double* out2,
                              cudaStream_t st) {
-  k_dA_times_W<<<(int)n, QT, 0, st>>>(At, A, W, ld, n, Q);
+  k_rows_times_W<<<(int)n, QT, 0, st>>>(At, A, W, ld, n, np, 1.0, 0, Q, nullptr);
   LAUNCH_CHECK();
   const int nt = np / 32;
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
@@ -410,6 +443,19 @@ void logdet_difference_terms(const double* At, const double* A, const double* W,
   k_trace_pairs<<<g, RT, 0, st>>>(Q, ld, n, np, parts);
   LAUNCH_CHECK();
   k_finalize<<<1, RT, 0, st>>>(parts, g, 2, out2);
+  LAUNCH_CHECK();
+}
+
+void inverse_residual(const double* A, const double* W, int64_t ld, int64_t n, int np, double* R,
+                      double* rmax, cudaStream_t st) {
+  CUDA_CHECK(cudaMemsetAsync(rmax, 0, sizeof(double), st));
+  k_rows_times_W<<<np, QT, 0, st>>>(A, nullptr, W, ld, n, np, -1.0, 1, R, rmax);
+  LAUNCH_CHECK();
+}
+
+void add_lower_mirror(double* W, const double* C, int64_t ld, int np, cudaStream_t st) {
+  dim3 grid(np / 32, np / 32);
+  k_add_lower_mirror<<<grid, dim3(32, 8), 0, st>>>(W, C, ld, np);
   LAUNCH_CHECK();
 }
 

@@ -31,6 +31,12 @@ void objective_terms(const double* S, const double* A, int64_t ld, int64_t n, do
 void logdet_difference_terms(const double* At, const double* A, const double* W, int64_t ld,
                              int64_t n, int np, double* Q, double* parts, double* out2,
                              cudaStream_t st);
+// R = I - A W in FP64 over the padded size (padding of R zero), with the nonzeros of each
+// row of A compacted first; *rmax = max |R_ij| over the n x n block.
+void inverse_residual(const double* A, const double* W, int64_t ld, int64_t n, int np, double* R,
+                      double* rmax, cudaStream_t st);
+// lower(W) += lower(C), then W's upper triangle := its lower triangle transposed.
+void add_lower_mirror(double* W, const double* C, int64_t ld, int np, cudaStream_t st);
 void unpad(const double* src, int64_t ld, int64_t n, double* dst, cudaStream_t st);
 void unpad_i8(const int8_t* src, int64_t ld, int64_t n, int8_t* dst, cudaStream_t st);
 void pad_i8(const int8_t* src, int64_t n, int8_t* dst, int64_t ld, cudaStream_t st);

@@ -122,6 +122,82 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
 }
 
 // ------------------------------------------------------------------------------------------
+// launch counting and profiling
+// ------------------------------------------------------------------------------------------
+thread_local int64_t tl_launches = 0;
+int64_t thread_launches() { return tl_launches; }
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CUDA_CHECK(cudaEventCreate(&e));
+  return e;
+}
+void Profiler::start() {
+  for (auto& r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+  recs.clear();
+  on = true;
+}
+void Profiler::begin_rec(int cls, double work, cudaStream_t st, Rec& r) {
+  r.cls = -1;
+  if (!on) return;
+  r.cls = cls;
+  r.work = work;
+  r.a = get();
+  r.b = get();
+  CUDA_CHECK(cudaEventRecord(r.a, st));
+}
+void Profiler::end_rec(Rec& r, cudaStream_t st) {
+  if (r.cls < 0) return;
+  CUDA_CHECK(cudaEventRecord(r.b, st));
+  recs.push_back(r);
+}
+void Profiler::collect(glasso_profile* out) {
+  std::memset(out, 0, sizeof(*out));
+  for (auto& r : recs) {
+    CUDA_CHECK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, r.a, r.b));
+    out->ms[r.cls] += ms;
+    out->work[r.cls] += r.work;
+    out->launches[r.cls] += 1;
+  }
+  for (auto& r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+  recs.clear();
+  on = false;
+}
+Profiler::~Profiler() {
+  for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+namespace {
+// algorithmic FLOPs of one product with the structure the call declares
+double gemm_flops(const GemmArgs& a) {
+  const double M = a.M, N = a.N, K = a.K;
+  switch (a.krule) {
+    case KR_LO_COL: return M * N * (N + 1.0);                 // B lower triangular (K = N)
+    case KR_HI_ROW: return N * M * (M + 1.0);                 // A lower triangular (K = M)
+    case KR_LO_ROW: return K * K * K / 3.0 + K * K;           // X^T X, X lower, lower output
+    default: return a.lower ? M * (M + 1.0) * K : 2.0 * M * N * K;
+  }
+}
+int prof_class(GemmRole r) {
+  switch (r) {
+    case GemmRole::Sandwich: return GLASSO_PROF_SANDWICH;
+    case GemmRole::Trailing: return GLASSO_PROF_TRAILING;
+    case GemmRole::Panel: return GLASSO_PROF_PANEL;
+    case GemmRole::Inverse: return GLASSO_PROF_INVERSE;
+    default: return GLASSO_PROF_REFINE;
+  }
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
 // engine
 // ------------------------------------------------------------------------------------------
 Engine::Engine(const glasso_config& cfg) : cfg_(cfg) {
@@ -143,13 +219,16 @@ Engine::~Engine() {
 }
 
 void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
+  Profiler::Rec rec;
+  prof.begin_rec(prof_class(role), gemm_flops(a), st, rec);
   const bool mixed = cfg_.precision != GLASSO_FP64;
   if (mixed && role != GemmRole::Panel && tc_gemm_supported(a)) {
     tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
             ws.tc_scratch, ws.tc_scratch_bytes, st);
-    return;
+  } else {
+    gemm_f64(a, 1, st);
   }
-  gemm_f64(a, 1, st);
+  prof.end_rec(rec, st);
 }
 
 GemmFn Engine::gemm_fn() {
@@ -159,6 +238,8 @@ GemmFn Engine::gemm_fn() {
 void Engine::sync_scalars() {
   CUDA_CHECK(cudaMemcpyAsync(ws.hs, ws.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
   CUDA_CHECK(cudaStreamSynchronize(stream_));
+  if (cfg_.precision != GLASSO_FP64 && tc_error_flag(stream_))
+    throw Error(GLASSO_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting on its pipeline");
 }
 
 // Copy a caller matrix (n x n, leading dim n) into dst (padded), mirroring its lower
@@ -200,7 +281,28 @@ void Engine::load_matrix(const void* src, bool f32, bool on_device, int64_t n, d
 
 void Engine::compute_inverse(const double* L, const double* Dinv, cudaStream_t st) {
   inverse_from_factor(L, Dinv, ws.ld, ws.np, ws.X, ws.T, ws.W, gemm_fn(), st);
-  if (cfg_.precision != GLASSO_FP64) refine_inverse(*this, L, st);
+  if (cfg_.precision != GLASSO_FP64) refine_inverse(st);
+}
+
+// Mixed mode: Newton-Schulz sweeps W <- W + W R, R = I - A W formed in FP64 from the sparse
+// rows of A; the correction product runs on the tensor cores (its error is |R| times the
+// split-precision error).  Stops once max |R_ij| < 1e-14 (at most three sweeps).
+void Engine::refine_inverse(cudaStream_t st) {
+  const int np = ws.np;
+  const int64_t ld = ws.ld;
+  double* rmax = &ws.sc->aux[0];
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    inverse_residual(ws.A, ws.W, ld, ws.n, np, ws.X, rmax, st);
+    double h = 0.0;
+    CUDA_CHECK(cudaMemcpyAsync(&h, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    ws.hs->aux[1 + sweep] = h;
+    if (h < 1e-14) break;
+    GemmArgs g = gemm_args(ws.W, ld, 0, ws.X, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
+    g.lower = 1;
+    gemm(g, GemmRole::Refine, st);
+    add_lower_mirror(ws.W, ws.Y, ld, np, st);
+  }
 }
 
 // Y = lower(A X A): T = A X, then Y = T A on the lower triangle (Y is symmetric)
@@ -222,18 +324,21 @@ double Engine::power_lambda_max(const double* M, cudaStream_t st) {
   LAUNCH_CHECK();
   for (int it = 0; it < 60; ++it) {
     k_gemv_rows<<<(int)n, 256, 0, st>>>(M, ws.ld, n, x, y);
+    LAUNCH_CHECK();
     k_normalize<<<1, 1024, 0, st>>>(y, n, x, nrm);
+    LAUNCH_CHECK();
   }
-  LAUNCH_CHECK();
   double h = 0.0;
   CUDA_CHECK(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
   return h;
 }
 
-SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n, double lam,
-                       double tol, const double* theta0, double* theta_out, bool keep_trace) {
-  const auto t_begin = std::chrono::steady_clock::now();
+void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, double lam,
+                   const double* theta0) {
+  st_ = SolveState{};
+  st_.t_begin = std::chrono::steady_clock::now();
+  st_.launches_begin = tl_launches;
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   cudaStream_t st = stream_;
@@ -241,10 +346,6 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
   const int64_t ld = ws.ld;
   const size_t mat = sizeof(double) * ld * np;
   Scalars& h = *ws.hs;
-  const double shrink = cfg_.shrink > 0 && cfg_.shrink < 1 ? cfg_.shrink : 0.5;
-  const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
-  const int max_iter = cfg_.max_iter > 0 ? cfg_.max_iter : 500;
-
   load_matrix(Sin, s_f32, s_on_device, n, ws.S, true);
   CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ld * np, st));
   CUDA_CHECK(cudaMemsetAsync(ws.X, 0, mat, st));
@@ -258,6 +359,7 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
   // factor the start point
   CUDA_CHECK(cudaMemcpyAsync(ws.Lt, ws.A, mat, cudaMemcpyDeviceToDevice, st));
   k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  LAUNCH_CHECK();
   cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
   objective_terms(ws.S, ws.A, ld, n, ws.parts, &ws.sc->trsa, st);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -265,76 +367,112 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
   if (!h.pd_t) throw Error(GLASSO_ERR_NOT_PD, "the start point is not positive definite");
   std::swap(ws.L, ws.Lt);
   std::swap(ws.Dinv, ws.Dinv_t);
-  double ld_A = h.logdet_t, trsa = h.trsa, l1 = h.l1;
-  double F = -ld_A + trsa + lam * l1;
+  st_.active = true;
+  st_.on_device = s_on_device;
+  st_.n = n;
+  st_.lam = lam;
+  st_.ld_A = h.logdet_t;
+  st_.trsa = h.trsa;
+  st_.l1 = h.l1;
+  st_.F = -st_.ld_A + st_.trsa + lam * st_.l1;
+}
 
-  SolveOut out;
-  int k = 0;
-  for (;;) {
-    compute_inverse(ws.L, ws.Dinv, st);
+int Engine::step(double tol, int max_iter, bool keep_trace) {
+  if (!st_.active) throw Error(GLASSO_ERR_ARG, "no solve in progress (call glasso_begin)");
+  cudaStream_t st = stream_;
+  const int np = ws.np;
+  const int64_t ld = ws.ld, n = st_.n;
+  const double lam = st_.lam;
+  Scalars& h = *ws.hs;
+  SolveOut& out = st_.out;
+  const double shrink = cfg_.shrink > 0 && cfg_.shrink < 1 ? cfg_.shrink : 0.5;
+  const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
+
+  compute_inverse(ws.L, ws.Dinv, st);
+  {
+    Profiler::Rec rec;
+    prof.begin_rec(GLASSO_PROF_GRADIENT, 33.0 * (double)n * (double)n, st, rec);
     gradient(ws.S, ws.W, ws.A, ld, n, lam, ws.X, ws.code, ld, ws.parts, &ws.sc->z_l1, st);
-    sync_scalars();
-    out.r = h.z_l1 / h.a_l1;
-    out.z_fro = std::sqrt(h.z_fro2);
-    out.nnz = h.nnz;
-    if (out.r <= tol) { out.status = GLASSO_OK; break; }
-    if (k >= max_iter) { out.status = GLASSO_MAX_ITER; break; }
-    sandwich(st);
-    const double delta = 16.0 * kUnitRoundoff * (std::fabs(ld_A) + std::fabs(trsa) + lam * l1);
-    double t = 1.0, dF = INFINITY;
-    int trials = 0, tier = 1;
-    bool accepted = false;
-    auto try_step = [&](double tt) -> double {
+    prof.end_rec(rec, st);
+  }
+  sync_scalars();
+  out.r = h.z_l1 / h.a_l1;
+  out.z_fro = std::sqrt(h.z_fro2);
+  out.nnz = h.nnz;
+  if (out.r <= tol) return GLASSO_OK;
+  if (st_.k >= max_iter) return GLASSO_MAX_ITER;
+  sandwich(st);
+  // rounding allowance of F: FP64 unit roundoff, or the split products' for the mixed modes
+  // (whose Cholesky trailing updates carry about 2^-21 relative error)
+  const double u = cfg_.precision == GLASSO_FP64 ? kUnitRoundoff : std::ldexp(1.0, -21);
+  const double delta = 16.0 * u * (std::fabs(st_.ld_A) + std::fabs(st_.trsa) + lam * st_.l1);
+  double t = 1.0, dF = INFINITY;
+  int trials = 0, tier = 1;
+  bool accepted = false;
+  auto try_step = [&](double tt) -> double {
+    {
+      Profiler::Rec rec;
+      prof.begin_rec(GLASSO_PROF_TRIAL, 24.5 * (double)n * (double)n, st, rec);
       trial(ws.A, ws.Y, ws.code, ld, ws.S, ld, n, np, lam, tt, ws.At, ws.Lt, ws.parts,
             &ws.sc->lin_s, st);
-      k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
-      cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
-      CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+      prof.end_rec(rec, st);
+    }
+    k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+    LAUNCH_CHECK();
+    cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+    CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    sync_scalars();
+    ++trials;
+    tier = 1;
+    if (!h.pd_t) return INFINITY;
+    const double lin = h.lin_s + lam * h.lin_l1;
+    double d = -(h.logdet_t - st_.ld_A) + lin;
+    if (std::fabs(d) <= kDiffBand * delta) {
+      // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3)
+      logdet_difference_terms(ws.At, ws.A, ws.W, ld, n, np, ws.T, ws.parts, &ws.sc->tr_e, st);
       sync_scalars();
-      ++trials;
-      tier = 1;
-      if (!h.pd_t) return INFINITY;
-      const double lin = h.lin_s + lam * h.lin_l1;
-      double d = -(h.logdet_t - ld_A) + lin;
-      if (std::fabs(d) <= kDiffBand * delta) {
-        // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3)
-        logdet_difference_terms(ws.At, ws.A, ws.W, ld, n, np, ws.T, ws.parts, &ws.sc->tr_e, st);
-        sync_scalars();
+      // the series is used while |E|_F <= 0.1, where its truncation (<= |E|_F^3 / 2.7) stays
+      // far below the second-order term; otherwise the Cholesky difference stands
+      if (h.tr_e2 <= 0.01) {
         d = -(h.tr_e - 0.5 * h.tr_e2) + lin;
         tier = 2;
       }
-      return d;
-    };
-    while (t >= t_min) {
-      dF = try_step(t);
-      if (dF < 0.0) { accepted = true; break; }
-      t *= shrink;
     }
-    if (!accepted) {
-      const double lmax_a = power_lambda_max(ws.A, st);
-      const double lmax_w = power_lambda_max(ws.W, st);
-      t = std::pow(kFallbackFactor / (lmax_a * lmax_w), 2.0);
-      dF = try_step(t);
-      accepted = dF < 0.0;
-    }
-    out.trials += trials;
-    if (keep_trace)
-      out.trace.push_back(IterRecord{k, trials, tier, F, out.r, out.z_fro, out.nnz, t, dF});
-    if (!accepted) { out.status = GLASSO_LINESEARCH_STALL; break; }
-    std::swap(ws.A, ws.At);
-    std::swap(ws.L, ws.Lt);
-    std::swap(ws.Dinv, ws.Dinv_t);
-    ld_A = h.logdet_t;
-    trsa = h.trsa_t;
-    l1 = h.l1_t;
-    F = -ld_A + trsa + lam * l1;
-    ++k;
+    return d;
+  };
+  while (t >= t_min) {
+    dF = try_step(t);
+    if (dF < 0.0) { accepted = true; break; }
+    t *= shrink;
   }
-  out.iterations = k;
-  out.F = F;
-  out.logdet = ld_A;
+  if (!accepted) {
+    const double lmax_a = power_lambda_max(ws.A, st);
+    const double lmax_w = power_lambda_max(ws.W, st);
+    t = std::pow(kFallbackFactor / (lmax_a * lmax_w), 2.0);
+    dF = try_step(t);
+    accepted = dF < 0.0;
+  }
+  out.trials += trials;
+  if (keep_trace)
+    out.trace.push_back(IterRecord{st_.k, trials, tier, st_.F, out.r, out.z_fro, out.nnz, t, dF});
+  if (!accepted) return GLASSO_LINESEARCH_STALL;
+  std::swap(ws.A, ws.At);
+  std::swap(ws.L, ws.Lt);
+  std::swap(ws.Dinv, ws.Dinv_t);
+  st_.ld_A = h.logdet_t;
+  st_.trsa = h.trsa_t;
+  st_.l1 = h.l1_t;
+  st_.F = -st_.ld_A + st_.trsa + lam * st_.l1;
+  ++st_.k;
+  return -1;
+}
+
+SolveOut Engine::finish(double* theta_out) {
+  if (!st_.active) throw Error(GLASSO_ERR_ARG, "no solve in progress (call glasso_begin)");
+  cudaStream_t st = stream_;
+  const int64_t n = st_.n, ld = ws.ld;
   if (theta_out) {
-    if (s_on_device) {
+    if (st_.on_device) {
       unpad(ws.A, ld, n, theta_out, st);
     } else {
       unpad(ws.A, ld, n, ws.T, st);
@@ -342,7 +480,25 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
     }
   }
   CUDA_CHECK(cudaStreamSynchronize(st));
-  out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_begin).count();
+  SolveOut out = std::move(st_.out);
+  out.iterations = st_.k;
+  out.F = st_.F;
+  out.logdet = st_.ld_A;
+  out.launches = tl_launches - st_.launches_begin;
+  out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - st_.t_begin).count();
+  st_.active = false;
+  return out;
+}
+
+SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n, double lam,
+                       double tol, const double* theta0, double* theta_out, bool keep_trace) {
+  const int max_iter = cfg_.max_iter > 0 ? cfg_.max_iter : 500;
+  begin(Sin, s_f32, s_on_device, n, lam, theta0);
+  int status;
+  while ((status = step(tol, max_iter, keep_trace)) < 0) {
+  }
+  SolveOut out = finish(theta_out);
+  out.status = status;
   return out;
 }
 
@@ -356,6 +512,7 @@ void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double*
   load_matrix(A, false, true, n, ws.Lt, false);
   pad_identity(ws.Lt, ws.ld, n, ws.np, st);
   k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  LAUNCH_CHECK();
   cholesky_f64(ws.Lt, ws.ld, ws.np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
   k_unpad_lower<<<red_blocks(n), 256, 0, st>>>(ws.Lt, ws.ld, n, L);
@@ -373,6 +530,7 @@ int Engine::op_inverse(const double* A, int64_t n, double* W) {
   pad_identity(ws.A, ws.ld, n, ws.np, st);
   CUDA_CHECK(cudaMemcpyAsync(ws.L, ws.A, sizeof(double) * ws.ld * ws.np, cudaMemcpyDeviceToDevice, st));
   k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  LAUNCH_CHECK();
   cholesky_f64(ws.L, ws.ld, ws.np, ws.Dinv, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
   sync_scalars();

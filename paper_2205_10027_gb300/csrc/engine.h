@@ -48,8 +48,40 @@ struct SolveOut {
   int status = 0;
   int iterations = 0, trials = 0;
   double r = 0, z_fro = 0, F = 0, logdet = 0, nnz = 0, seconds = 0;
+  int64_t launches = 0;
   std::vector<IterRecord> trace;
 };
+
+// Iterate and objective pieces carried between outer iterations.
+struct SolveState {
+  bool active = false;
+  bool on_device = false;
+  int64_t n = 0;
+  double lam = 0, ld_A = 0, trsa = 0, l1 = 0, F = 0;
+  int k = 0;
+  SolveOut out;
+  std::chrono::steady_clock::time_point t_begin;
+  int64_t launches_begin = 0;
+};
+
+// CUDA-event accounting of the kernel classes (glasso_profile_*).
+struct Profiler {
+  bool on = false;
+  struct Rec { int cls; double work; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void start();
+  void begin_rec(int cls, double work, cudaStream_t st, Rec& r);
+  void end_rec(Rec& r, cudaStream_t st);
+  void collect(glasso_profile* out);
+  ~Profiler();
+};
+
+double probe_fp64_tflops(int device);
+
+// Kernel launches made by the calling thread (each engine runs on one thread at a time).
+int64_t thread_launches();
 
 class Engine {
  public:
@@ -61,6 +93,13 @@ class Engine {
   // Full pISTA solve.  S is the caller's n x n matrix (host or device); theta0 may be null.
   SolveOut solve(const void* S, bool s_f32, bool s_on_device, int64_t n, double lam, double tol,
                  const double* theta0, double* theta_out, bool keep_trace = false);
+  // The same solve one outer iteration at a time.
+  void begin(const void* S, bool s_f32, bool s_on_device, int64_t n, double lam, const double* theta0);
+  // Returns -1 after an accepted step, else the final status (OK, MAX_ITER, STALL).
+  int step(double tol, int max_iter, bool keep_trace);
+  SolveOut finish(double* theta_out);
+  const SolveState& state() const { return st_; }
+  Profiler prof;
 
   // single steps on caller device arrays (leading dimension n)
   void op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet);
@@ -81,10 +120,12 @@ class Engine {
   void load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst, bool check_s);
   void sandwich(cudaStream_t st);
   void compute_inverse(const double* L, const double* Dinv, cudaStream_t st);
+  void refine_inverse(cudaStream_t st);
   double power_lambda_max(const double* M, cudaStream_t st);
   void sync_scalars();
 
   glasso_config cfg_;
+  SolveState st_;
   cudaStream_t stream_ = nullptr;
   bool own_stream_ = false;
 };

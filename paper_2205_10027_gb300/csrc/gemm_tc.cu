@@ -1,13 +1,406 @@
-// Split-precision tensor-core GEMM (placeholder until the tcgen05 kernel lands).
+// Split-precision dense products on the 5th-generation tensor cores.
+//
+// Each FP64 operand is split into hi + lo parts of a narrow type (TF32 or BF16); the product
+// op(A) op(B) is formed as hi*hi + hi*lo + lo*hi by tcgen05.mma with FP32 accumulation in
+// TMEM, and the epilogue adds alpha * acc to beta * C in FP64.  One CTA computes a
+// 128 x 128 output tile: one thread issues TMA loads of the four 128 x (128 bytes) operand
+// tiles of a k-stage into a 3-stage shared-memory ring (128-byte swizzle), one thread issues
+// the MMAs, and all four warps drain the accumulator with tcgen05.ld.  Every wait on an
+// mbarrier is bounded; on a timeout the CTA records an error and leaves without writing.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include "engine.h"
 #include "gemm_tc.h"
 
 namespace glasso {
-size_t tc_scratch_bytes_for(int) { return 0; }
-bool tc_gemm_supported(const GemmArgs&) { return false; }
-void tc_gemm(const GemmArgs&, TcKind, void*, size_t, cudaStream_t) {
-  throw Error(GLASSO_ERR_UNSUPPORTED, "tensor-core GEMM not available");
+
+namespace {
+constexpr int TM = 128, TN = 128;
+constexpr int STAGES = 3;
+constexpr int THREADS = 128;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr int TILE_BYTES = 128 * 128;          // 128 rows x 128 bytes of K
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at 2 GHz
+
+struct TcArgs {
+  double* C;
+  int64_t ldc;
+  int M, N, K;
+  double alpha, beta;
+  int lower, krule;
+  int kstep;          // K elements per 128-byte stage: 32 (TF32) or 64 (BF16)
+  uint32_t idesc;     // tcgen05 instruction descriptor
+  const int* flag;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-void refine_inverse(Engine&, const double*, cudaStream_t) {}
-bool tc_available() { return false; }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Wait for the phase with the given parity to complete; false after WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout:
+// rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                    uint32_t accumulate, bool tf32) {
+  if (tf32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+              const __grid_constant__ TcArgs p) {
+  if (p.flag && *p.flag == 0) return;
+  const int tm = blockIdx.y, tn = blockIdx.x;
+  const int row0 = tm * TM, col0 = tn * TN;
+  if (p.lower && row0 + TM <= col0) return;  // tile entirely above the diagonal
+  int k_lo = 0, k_hi = p.K;
+  if (p.krule == KR_LO_COL) k_lo = col0;
+  else if (p.krule == KR_LO_ROW) k_lo = row0;
+  else if (p.krule == KR_HI_ROW) k_hi = min(p.K, row0 + TM);
+  k_lo = (k_lo / p.kstep) * p.kstep;
+  const int nk = k_hi > k_lo ? (k_hi - k_lo + p.kstep - 1) / p.kstep : 0;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const bool tf32 = p.kstep == 32;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    // producer: TMA loads of the four operand tiles of each k-stage
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+      if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) { *s_abort = 1; break; }
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      const int kx = k_lo + i * p.kstep;
+      tma_load_2d(st, &mAh, &full[s], kx, row0);
+      tma_load_2d(st + TILE_BYTES, &mAl, &full[s], kx, row0);
+      tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full[s], kx, col0);
+      tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full[s], kx, col0);
+      ++issued;
+    }
+    // do not leave while loads may still land in shared memory
+    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
+      if (!*s_abort) break;
+      mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    // MMA issuer: 4 instructions of 32 bytes along K per stage, three products each
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) { *s_abort = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ah = sw128_desc(base + kk * 32);
+        const uint64_t al = sw128_desc(base + TILE_BYTES + kk * 32);
+        const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
+        const uint64_t bl = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+        mma(tmem, al, bh, p.idesc, (i | kk) != 0, tf32);
+        mma(tmem, ah, bl, p.idesc, 1, tf32);
+        mma(tmem, ah, bh, p.idesc, 1, tf32);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncthreads();
+
+  // epilogue: thread (warp w, lane l) owns row 32 w + l of the tile
+  bool ok = !*s_abort;
+  if (ok && nk > 0) ok = mbar_wait(done, 0);
+  ok = __syncthreads_and(ok);  // uniform: tcgen05.ld below is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int r = row0 + warp * 32 + lane;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(p.err, 1);
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < TN / 32; ++c) {
+      float v[32];
+      if (nk > 0) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
+      if (r < p.M) {
+        double* dst = p.C + (int64_t)r * p.ldc + col0 + c * 32;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = col0 + c * 32 + j;
+          if (col >= p.N || (p.lower && col > r)) continue;
+          const double a = p.alpha * (double)v[j];
+          dst[j] = (p.beta == 0.0) ? a : fma(p.beta, dst[j], a);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- operand splitting: out[r][c] = op[r][c], op = src or its transpose, into hi + lo parts
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+
+template <bool BF16>
+__global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, int cols, int trans,
+                        void* __restrict__ hi, void* __restrict__ lo, int64_t ldo) {
+  __shared__ double t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    // load the (r0, c0) tile of op: element (r0 + i, c0 + tx) of op
+    double v = 0.0;
+    if (!trans) {
+      const int rr = r0 + i, cc = c0 + tx;
+      if (rr < rows && cc < cols) v = src[(int64_t)rr * lds + cc];
+      t[i][tx] = v;
+    } else {
+      // op[r][c] = src[c][r]: read src row c0 + i, columns r0 + tx (coalesced)
+      const int sr = c0 + i, sc = r0 + tx;
+      if (sr < cols && sc < rows) v = src[(int64_t)sr * lds + sc];
+      t[tx][i] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int rr = r0 + i, cc = c0 + tx;
+    if (rr >= rows || cc >= cols) continue;
+    const double x = t[i][tx];
+    const int64_t o = (int64_t)rr * ldo + cc;
+    if (BF16) {
+      const __nv_bfloat16 h = __double2bfloat16(x);
+      const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+      reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
+      reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+    } else {
+      const float h = tf32_round((float)x);
+      const float l = tf32_round((float)(x - (double)h));
+      reinterpret_cast<float*>(hi)[o] = h;
+      reinterpret_cast<float*>(lo)[o] = l;
+    }
+  }
+}
+
+// ---- host side --------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D map over a rows x cols array (row stride ld elements) with 128 x (128 bytes) boxes
+CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld) {
+  CUtensorMap m;
+  const int esz = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), 128};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                 base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(GLASSO_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+void split(const double* src, int64_t lds, int rows, int cols, bool trans, bool bf16, void* hi, void* lo,
+           int64_t ldo, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  if (bf16)
+    k_split<true><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, trans, hi, lo, ldo);
+  else
+    k_split<false><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, trans, hi, lo, ldo);
+  LAUNCH_CHECK();
+}
+
+int* g_err = nullptr;  // device error word of the tensor-core kernels
+}  // namespace
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+size_t tc_scratch_bytes_for(int np) { return (size_t)4 * np * np * sizeof(float) + 256; }
+
+bool tc_gemm_supported(const GemmArgs& a) {
+  // 128-row tiles; smaller products stay on the FP64 kernel
+  return a.M % 64 == 0 && a.N % 64 == 0 && a.K % 64 == 0 && a.M >= 128 && a.N >= 128 && a.K >= 64;
+}
+
+int tc_error_flag(cudaStream_t st) {
+  if (!g_err) return 0;
+  int h = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return h;
+}
+
+void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  const bool bf16 = kind == TcKind::BF16x3;
+  const size_t esz = bf16 ? 2 : 4;
+  const size_t need = esz * ((size_t)2 * a.M * a.K + (size_t)2 * a.N * a.K);
+  if (need + 256 > scratch_bytes) throw Error(GLASSO_ERR_OOM, "tensor-core scratch too small");
+  static std::once_flag once;
+  std::call_once(once, [] {
+    CUDA_CHECK(cudaMalloc(&g_err, sizeof(int)));
+    CUDA_CHECK(cudaMemset(g_err, 0, sizeof(int)));
+    CUDA_CHECK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  });
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  void* Ah = base;
+  void* Al = base + esz * (size_t)a.M * a.K;
+  void* Bh = base + esz * (size_t)2 * a.M * a.K;
+  void* Bl = base + esz * ((size_t)2 * a.M * a.K + (size_t)a.N * a.K);
+  // A part: [M][K] = op(A); B part: [N][K] = op(B)^T
+  split(a.A, a.lda, a.M, a.K, a.transA != 0, bf16, Ah, Al, a.K, st);
+  split(a.B, a.ldb, a.N, a.K, a.transB == 0, bf16, Bh, Bl, a.K, st);
+  const CUtensorMap mAh = make_map(Ah, bf16, a.M, a.K, a.K), mAl = make_map(Al, bf16, a.M, a.K, a.K);
+  const CUtensorMap mBh = make_map(Bh, bf16, a.N, a.K, a.K), mBl = make_map(Bl, bf16, a.N, a.K, a.K);
+  TcArgs p;
+  p.C = a.C;
+  p.ldc = a.ldc;
+  p.M = a.M;
+  p.N = a.N;
+  p.K = a.K;
+  p.alpha = a.alpha;
+  p.beta = a.beta;
+  p.lower = a.lower;
+  p.krule = a.krule;
+  p.kstep = bf16 ? 64 : 32;
+  const uint32_t ab = bf16 ? 1u : 2u;  // operand format: BF16 = 1 (kind::f16), TF32 = 2 (kind::tf32)
+  p.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  p.flag = a.flag;
+  p.err = g_err;
+  dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM);
+  k_gemm_tc<<<grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
+  LAUNCH_CHECK();
+}
+
 }  // namespace glasso

@@ -15,7 +15,9 @@ bool tc_gemm_supported(const GemmArgs& a);
 // C = alpha op(A) op(B) + beta C with each FP64 operand split into hi + lo parts and the
 // three products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, then added to C in FP64.
 void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st);
-// Mixed mode: one Newton-Schulz sweep W <- W + W (I - A W) with the residual in FP64.
-void refine_inverse(Engine& e, const double* L, cudaStream_t st);
+// Whether the driver exposes what the tensor-core path needs (TMA descriptor encoding).
+bool tc_available();
+// 1 if a tensor-core kernel timed out waiting on one of its barriers (synchronises st).
+int tc_error_flag(cudaStream_t st);
 
 }  // namespace glasso

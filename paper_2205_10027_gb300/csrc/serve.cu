@@ -26,6 +26,7 @@ void to_result(glasso_result* r, const SolveOut& o) {
   r->objective = o.F;
   r->logdet = o.logdet;
   r->seconds = o.seconds;
+  r->kernel_launches = o.launches;
 }
 }  // namespace
 

@@ -171,3 +171,30 @@ def test_monotone_pd_kkt_certificate_n600(fp64):
     r = np.sum(np.abs(Z)) / np.sum(np.abs(theta))
     assert r <= 2e-9
     assert abs(res["rel_kkt_l1"] - r) <= 1e-3 * r + 1e-14
+
+
+def test_stepwise_equals_solve(fp64, glasso):
+    p = inputs.chain_n100()
+    theta, res = fp64.solve(p.S, p.lam, p.tol)
+    fp64.begin(p.S, p.lam)
+    steps = 0
+    while True:
+        st, r = fp64.step(p.tol)
+        assert r["kernel_launches"] > 0
+        if st != glasso.PENDING:
+            break
+        steps += 1
+    out = np.empty_like(p.S)
+    fp64.end(out)
+    assert st == glasso.OK and steps == res["iterations"]
+    assert np.array_equal(out, theta)
+    assert res["kernel_launches"] > 0
+
+
+def test_profile_accounts_kernel_classes(fp64):
+    p = inputs.grid_n10000(side=12, m=30)
+    fp64.profile_start()
+    fp64.solve(p.S, p.lam, 1e-6)
+    prof = fp64.profile_stop()
+    for cls in ("sandwich", "trailing", "inverse", "gradient", "trial"):
+        assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
