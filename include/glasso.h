@@ -239,6 +239,33 @@ glasso_status glasso_op_trial(glasso_handle* h, const double* A, const double* Y
                               const int8_t* code, int64_t n, double lambda, double t,
                               double* At);
 
+/* ---- allocation-free variant of the gradient step ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory themselves -- code running under a framework that owns every device
+ * allocation, a stream-ordered runtime that forbids cudaMalloc on its hot path, or an
+ * embedding with a memory budget fixed in advance.  It computes what glasso_op_gradient
+ * computes, with no handle and no allocation: no cudaMalloc, cudaFree or allocating library
+ * call.  Its only scratch is a file-scope device array of GLASSO_NOALLOC_MAX_N * 4 doubles
+ * (512 KB) inside the library, which every GPU that loads the library holds until the
+ * process exits.
+ *   S, A, W   device pointers, n x n FP64 row-major, leading dimension n (no padding).
+ *   X, code   device outputs, n x n (FP64 and int8): X = (g + lambda G).M, code = G.M.
+ *   sums      device output of 4 doubles: ||Z||_1, ||A||_1, ||Z||_F^2, nnz(A).
+ *   stream    cudaStream_t to run on (NULL: the legacy default stream).
+ * Runs on the device that is current for the calling thread and returns once the work is
+ * queued on `stream` (the outputs are ready when the stream reaches it).  The first call on
+ * a device looks up the device address of the scratch array (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call on a device
+ * shares the one scratch array and overwrites its first n rows, so nothing in it has to
+ * start at zero; calls whose work overlaps on the GPU (different streams, or graphs replayed
+ * concurrently) race on it and must be serialised by the caller.
+ * Returns GLASSO_ERR_BUDGET when n > GLASSO_NOALLOC_MAX_N, GLASSO_ERR_ARG for NULL
+ * pointers, n < 1 or lambda <= 0, GLASSO_ERR_CUDA when a CUDA call fails. */
+#define GLASSO_NOALLOC_MAX_N 16384
+glasso_status glasso_gradient_noalloc(const double* S, const double* A, const double* W,
+                                      int64_t n, double lambda, double* X, int8_t* code,
+                                      double* sums, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

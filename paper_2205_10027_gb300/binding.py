@@ -84,6 +84,7 @@ _sig = {
     "glasso_profile_start": (C.c_int, [_h]),
     "glasso_profile_stop": (C.c_int, [_h, C.POINTER(glasso_profile)]),
     "glasso_probe_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "glasso_gradient_noalloc": (C.c_int, [_dp, _dp, _dp, C.c_int64, C.c_double, _dp, _dp, _dp, _dp]),
     "glasso_solve_batch": (C.c_int, [_h, C.POINTER(glasso_problem), C.c_int32, C.POINTER(glasso_result)]),
     "glasso_submit": (C.c_int, [_h, C.POINTER(glasso_request), C.POINTER(C.c_uint64)]),
     "glasso_poll": (C.c_int, [_h, C.c_uint64, C.POINTER(glasso_result), _dp]),
@@ -100,6 +101,7 @@ for _name, (_res, _args) in _sig.items():
     globals()[_name] = _f
 
 EXPORTED = tuple(_sig)
+NOALLOC_MAX_N = 16384  # GLASSO_NOALLOC_MAX_N
 
 
 class GlassoError(RuntimeError):
