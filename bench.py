@@ -87,6 +87,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(x: float) -> float:
+    """The maximum of a per-rank scalar over all ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, slowest_seconds: float) -> float:
+    """Whole-job rate: every rank processed units_per_rank; the job took the slowest rank's time."""
+    return world * units_per_rank / slowest_seconds
+
+
 def workload(side: int, m: int):
     from paper_2205_10027_gb300 import inputs
     return inputs.grid_n10000(side=side, m=m, seed=2, lam=0.1)
@@ -183,14 +200,10 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         prof = h.profile_stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1))
     last = res
     h.end()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
+    value = job_throughput(args.steps, world, ms / 1000.0)
 
     # ---- end to end through the public API, host buffers ------------------------------------
     S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
@@ -202,13 +215,9 @@ def run_ours(args):
     t0 = time.perf_counter()
     _, res_e2e = he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     he.close()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * res_e2e["iterations"] / e2e_s
+    e2e_value = job_throughput(res_e2e["iterations"], world, e2e_s)
 
     # ---- time to tolerance (device-resident) ---------------------------------------------------
     ttt = None
@@ -227,6 +236,7 @@ def run_ours(args):
         peaks, peak_kind = _peaks()
         # dominant kernel: the dense-product kernel (all GEMM classes are launches of it)
         gemm_cls = [c for c in ("sandwich", "trailing", "panel", "inverse", "refine") if c in prof]
+        # (the "factor" class spans whole factorisations and overlaps the GEMM classes)
         g_ms = sum(prof[c]["ms"] for c in gemm_cls)
         g_work = sum(prof[c]["work"] for c in gemm_cls)
         g_launch = sum(prof[c]["launches"] for c in gemm_cls)
@@ -280,6 +290,165 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_op(args):
+    """Micro-benchmark of one kernel class through its single-step entry point (the sandwich
+    products Y = Theta X Theta, or the Cholesky factorisation) at n = side^2, for profiling."""
+    import torch
+    from paper_2205_10027_gb300 import binding
+    p = workload(args.side, args.m)
+    n = p.S.shape[0]
+    rng = np.random.default_rng(0)
+    A = np.diag(1.0 / (np.diag(p.S) + p.lam))
+    X = rng.standard_normal((n, n))
+    X = 0.5 * (X + X.T)
+    Ad, Xd = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
+    Sd = torch.from_numpy(p.S + np.eye(n)).cuda()
+    h = binding.Handle(precision=args.precision)
+    fn = (lambda: h.op_sandwich(Ad, Xd)) if args.op == "sandwich" else (lambda: h.op_cholesky(Sd))
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    h.profile_start()
+    for _ in range(args.steps):
+        fn()
+    prof = h.profile_stop()
+    h.close()
+    out = {"op": args.op, "n": n, "precision": args.precision, "steps": args.steps}
+    for k, v in prof.items():
+        if v["ms"]:
+            out[k] = {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                      "tflops" if k not in ("gradient", "trial") else "gbs": v["work"] / (v["ms"] / 1e3) /
+                      (1e12 if k not in ("gradient", "trial") else 1e9)}
+    print(json.dumps(out))
+
+
+# Tables 1 and 2 of the paper (pISTA GPU column: seconds, iterations; RTX 2080 Ti, FP32 CuPy)
+PAPER_TABLES = {
+    1: dict(n=1000, rows=[("chain", 0.6, 0.04, 2.0), ("chain", 0.4, 0.10, 6.6), ("random", 0.6, 0.04, 2.2),
+                          ("random", 0.4, 0.10, 6.4), ("planar", 0.6, 0.03, 2.0), ("planar", 0.4, 0.24, 15.4)]),
+    2: dict(n=10000, rows=[("chain", 0.4, 5.69, 3.0), ("chain", 0.2, 12.89, 7.0), ("random", 0.4, 1.56, 0.6),
+                           ("random", 0.2, 5.67, 3.0), ("planar", 0.4, 3.92, 2.0), ("planar", 0.2, 20.91, 10.2)]),
+}
+
+
+def run_paper_table(args):
+    """The paper's own synthetic protocol (Sec. 6.1.1; m = 3% n, stop at 1e-2, samples
+    standardised), solved end to end from host S through glasso_solve, beside the printed
+    GPU numbers of Table 1 or 2."""
+    import torch
+    from paper_2205_10027_gb300 import binding, inputs
+    tab = PAPER_TABLES[args.paper_table]
+    n = tab["n"]
+    seeds = args.paper_seeds
+    h = binding.Handle(precision=args.precision, max_iter=1000)
+    rows = []
+    for kind, alpha, paper_s, paper_it in tab["rows"]:
+        times, its, nnz = [], [], []
+        for rep in range(seeds):
+            S = inputs.paper_protocol(kind, n, seed=300 + rep)
+            h.solve(S, alpha, 1e-2) if rep == 0 else None   # warm the workspace and graphs
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, res = h.solve(S, alpha, 1e-2)
+            times.append(time.perf_counter() - t0)
+            its.append(res["iterations"])
+            nnz.append(res["nnz"])
+        rows.append({"kind": kind, "alpha": alpha, "seconds": statistics.mean(times),
+                     "iterations": statistics.mean(its), "nnz": statistics.mean(nnz),
+                     "paper_seconds": paper_s, "paper_iterations": paper_it,
+                     "speedup_vs_paper": paper_s / statistics.mean(times)})
+    h.close()
+    print(json.dumps({"paper_table": args.paper_table, "n": n, "precision": args.precision, "seeds": seeds,
+                      "protocol": "m = 3% n, standardised samples, eps = 1e-2, start diag(1/(S_ii+alpha))",
+                      "timing": "glasso_solve from host S to host Theta, wall clock",
+                      "paper_hardware": "GeForce RTX 2080 Ti, FP32 (CuPy)", "rows": rows}))
+
+
+def run_batch(args):
+    """Batched regularisation paths: independent ER problems with n log-uniform in
+    [32, 1024], a descending lambda path of 8 values in [0.5, 0.02], warm-started, solved
+    concurrently through glasso_solve_batch.  Metric: solves per second."""
+    from paper_2205_10027_gb300 import binding, inputs
+    probs = inputs.batch_path_problems(count=args.batch_count, seed=3)
+    for p in probs:
+        p["tol"] = args.batch_tol
+    h = binding.Handle(precision=args.precision, serve_slots=args.slots, max_iter=args.batch_max_iter)
+    warm = inputs.batch_path_problems(count=min(4, len(probs)), seed=97)
+    for p in warm:
+        p["tol"] = args.batch_tol
+    h.solve_batch(warm)
+    t0 = time.perf_counter()
+    _, res = h.solve_batch(probs)
+    dt = time.perf_counter() - t0
+    h.close()
+    flat = [r for rs in res for r in rs]
+    print(json.dumps({"mode": "batch", "precision": args.precision, "problems": len(probs),
+                      "solves": len(flat), "seconds": dt, "solves_per_s": len(flat) / dt,
+                      "slots": args.slots, "tol": args.batch_tol, "max_iter": args.batch_max_iter,
+                      "converged": sum(r["status"] == 0 for r in flat),
+                      "iterations_total": sum(r["iterations"] for r in flat)}))
+
+
+def run_served(args):
+    """Served stream: Poisson arrivals, each request (S, lambda) from a pool of seeded chain /
+    grid datasets with n log-uniform in [64, n_max], lambda ~ U[0.05, 0.3], warm-started from
+    the nearest earlier lambda of the same dataset; requests are admitted by an HBM budget.
+    Reports p50 / p99 latency (submit to result) and solves/s, beside the same requests solved
+    one at a time in FP64."""
+    from paper_2205_10027_gb300 import binding, inputs
+    arrivals, ids, lams, pool = inputs.served_stream(count=args.served, rate_hz=args.rate, nmax=args.served_nmax)
+    cache = {}
+
+    def S_of(d):
+        if d not in cache:
+            cache[d] = inputs.served_dataset(pool[d])
+        return cache[d]
+
+    for d in sorted(set(ids.tolist())):
+        S_of(int(d))
+    h = binding.Handle(precision=args.precision, serve_slots=args.slots,
+                       hbm_budget_bytes=int(args.budget_gb * 1e9), max_iter=args.batch_max_iter)
+    t_start = time.perf_counter()
+    tickets = []
+    for a, d, lam in zip(arrivals, ids, lams):
+        now = time.perf_counter() - t_start
+        if a > now:
+            time.sleep(a - now)
+        tickets.append((h.submit(S_of(int(d)), float(lam), args.batch_tol, dataset_id=int(d)),
+                        S_of(int(d)).shape[0]))
+    lat, done = [], {}
+    while len(done) < len(tickets):
+        for t, n in tickets:
+            if t in done:
+                continue
+            st, res, _ = h.poll(t)
+            if st != binding.PENDING:
+                done[t] = res
+                lat.append(res["t_done"] - res["t_submit"])
+        time.sleep(0.001)
+    total = time.perf_counter() - t_start
+    h.close()
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    # one at a time in FP64 on a sample of the same requests
+    serial = None
+    if args.serial_sample:
+        hs = binding.Handle(precision="fp64", max_iter=args.batch_max_iter)
+        idx = np.linspace(0, len(ids) - 1, args.serial_sample).astype(int)
+        t0 = time.perf_counter()
+        for i in idx:
+            hs.solve(S_of(int(ids[i])), float(lams[i]), args.batch_tol)
+        serial = {"requests": len(idx), "seconds": time.perf_counter() - t0,
+                  "solves_per_s": len(idx) / (time.perf_counter() - t0)}
+        hs.close()
+    print(json.dumps({"mode": "served", "precision": args.precision, "requests": len(tickets),
+                      "rate_hz": args.rate, "n_max": args.served_nmax, "slots": args.slots,
+                      "seconds": total, "solves_per_s": len(tickets) / total,
+                      "p50_s": pct(0.50), "p99_s": pct(0.99),
+                      "converged": sum(r["status"] == 0 for r in done.values()),
+                      "serial_fp64_sample": serial}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,7 +461,34 @@ def main():
     ap.add_argument("--sample-side", type=int, default=50)
     ap.add_argument("--time-to-tol", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op", choices=["sandwich", "cholesky"], default=None,
+                    help="micro-benchmark one kernel class instead of the step")
+    ap.add_argument("--paper-table", type=int, choices=[1, 2], default=None,
+                    help="the paper's Table 1 or 2 protocol beside its printed GPU times")
+    ap.add_argument("--paper-seeds", type=int, default=3)
+    ap.add_argument("--batch", action="store_true", help="batched lambda paths (solves/s)")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-tol", type=float, default=1e-6)
+    ap.add_argument("--batch-max-iter", type=int, default=500)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--served", type=int, default=0, help="served stream of this many requests")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--served-nmax", type=int, default=4096)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--serial-sample", type=int, default=20)
     args = ap.parse_args()
+    if args.batch:
+        run_batch(args)
+        return
+    if args.served:
+        run_served(args)
+        return
+    if args.op:
+        run_op(args)
+        return
+    if args.paper_table:
+        run_paper_table(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -147,6 +147,8 @@ enum {
   GLASSO_PROF_REFINE = 4,     /* mixed mode: refinement products of W: FLOPs */
   GLASSO_PROF_GRADIENT = 5,   /* gradient / free-set / KKT pass: bytes moved */
   GLASSO_PROF_TRIAL = 6,      /* trial-point pass: bytes moved */
+  GLASSO_PROF_FACTOR = 7,     /* whole Cholesky-with-inverse calls (their products included):
+                                 FLOPs n^3/3 + n^3/3 */
   GLASSO_PROF_CLASSES = 8
 };
 

@@ -46,7 +46,7 @@ class glasso_result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PROF_CLASSES = ("sandwich", "trailing", "panel", "inverse", "refine", "gradient", "trial", "unused")
+PROF_CLASSES = ("sandwich", "trailing", "panel", "inverse", "refine", "gradient", "trial", "factor")
 
 
 class glasso_profile(C.Structure):

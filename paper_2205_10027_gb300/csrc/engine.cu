@@ -58,13 +58,12 @@ void dfree(T*& p) {
 // ------------------------------------------------------------------------------------------
 size_t Workspace::bytes_for(int np) {
   const size_t m = (size_t)np * np;
-  return 9 * m * sizeof(double) + m + 2 * (size_t)np * kNb * sizeof(double) +
-         tc_scratch_bytes_for(np);
+  return 11 * m * sizeof(double) + m + tc_scratch_bytes_for(np);
 }
 
 void Workspace::release() {
   dfree(S); dfree(A); dfree(At); dfree(W); dfree(L); dfree(Lt); dfree(X); dfree(Y); dfree(T);
-  dfree(code); dfree(Dinv); dfree(Dinv_t); dfree(ld_parts); dfree(parts); dfree(sc);
+  dfree(code); dfree(Li); dfree(Lti); dfree(ld_parts); dfree(parts); dfree(sc);
   dfree(pd); dfree(vmax); dfree(bad); dfree(vec);
   if (staging) cudaFree(staging);
   staging = nullptr;
@@ -98,7 +97,7 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
     };
     alloc(S, m * 8); alloc(A, m * 8); alloc(At, m * 8); alloc(W, m * 8); alloc(L, m * 8);
     alloc(Lt, m * 8); alloc(X, m * 8); alloc(Y, m * 8); alloc(T, m * 8); alloc(code, m);
-    alloc(Dinv, (size_t)np_new * kNb * 8); alloc(Dinv_t, (size_t)np_new * kNb * 8);
+    alloc(Li, m * 8); alloc(Lti, m * 8);
     alloc(ld_parts, (size_t)(np_new / kNb) * 8);
     alloc(parts, (size_t)8 * kRedBlocks * 8);
     alloc(sc, sizeof(Scalars));
@@ -115,6 +114,7 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
       throw Error(GLASSO_ERR_OOM, "cudaMallocHost failed");
     }
     cap_np = np_new;
+    ++epoch;
   }
   n = n_new;
   np = (int)round_up(n_new, kPad);
@@ -183,6 +183,7 @@ double gemm_flops(const GemmArgs& a) {
     case KR_LO_COL: return M * N * (N + 1.0);                 // B lower triangular (K = N)
     case KR_HI_ROW: return N * M * (M + 1.0);                 // A lower triangular (K = M)
     case KR_LO_ROW: return K * K * K / 3.0 + K * K;           // X^T X, X lower, lower output
+    case KR_HI_COL: return M * N * (N + 1.0);                 // op(B) upper triangular (K = N)
     default: return a.lower ? M * (M + 1.0) * K : 2.0 * M * N * K;
   }
 }
@@ -214,6 +215,8 @@ Engine::Engine(const glasso_config& cfg) : cfg_(cfg) {
 Engine::~Engine() {
   cudaSetDevice(cfg_.device);
   if (stream_) cudaStreamSynchronize(stream_);
+  drop_graphs();
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
   ws.release();
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
 }
@@ -222,7 +225,7 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
   Profiler::Rec rec;
   prof.begin_rec(prof_class(role), gemm_flops(a), st, rec);
   const bool mixed = cfg_.precision != GLASSO_FP64;
-  if (mixed && role != GemmRole::Panel && tc_gemm_supported(a)) {
+  if (mixed && tc_gemm_supported(a)) {
     tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
             ws.tc_scratch, ws.tc_scratch_bytes, st);
   } else {
@@ -279,29 +282,96 @@ void Engine::load_matrix(const void* src, bool f32, bool on_device, int64_t n, d
   }
 }
 
-void Engine::compute_inverse(const double* L, const double* Dinv, cudaStream_t st) {
-  inverse_from_factor(L, Dinv, ws.ld, ws.np, ws.X, ws.T, ws.W, gemm_fn(), st);
+// Cholesky factor and its inverse of the matrix held in L (overwritten), PD flag and log det
+// into the scalars.
+void Engine::factor_direct(double* L, double* Li, cudaStream_t st) {
+  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
+  LAUNCH_CHECK();
+  cholesky_inverse(L, Li, ws.ld, ws.np, ws.T, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st,
+                   cfg_.precision != GLASSO_FP64);
+  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+}
+
+void Engine::drop_graphs() {
+  for (auto& g : fgraphs_) cudaGraphExecDestroy(g.second.exec);
+  fgraphs_.clear();
+  fseen_.clear();
+}
+
+// The recursive factorisation is a fixed sequence of a few thousand launches for a given
+// size and pair of buffers, so from its second use it is replayed as a captured CUDA graph
+// (captured on a private stream, launched on the engine's stream).  Profiling runs it
+// directly so that every product gets its own events.
+void Engine::factor(double* L, double* Li, cudaStream_t st) {
+  if (prof.on) {
+    Profiler::Rec rec;
+    const double np3 = (double)ws.np * ws.np * ws.np;
+    prof.begin_rec(GLASSO_PROF_FACTOR, 2.0 * np3 / 3.0, st, rec);
+    factor_direct(L, Li, st);
+    prof.end_rec(rec, st);
+    return;
+  }
+  if (graph_epoch_ != ws.epoch) {
+    drop_graphs();
+    graph_epoch_ = ws.epoch;
+  }
+  const GraphKey key{L, Li, ws.np};
+  auto it = fgraphs_.find(key);
+  if (it == fgraphs_.end()) {
+    if (++fseen_[key] < 2) {  // the first use runs directly (one-time set-up happens there)
+      factor_direct(L, Li, st);
+      return;
+    }
+    if (!cap_stream_) CUDA_CHECK(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    const int64_t l0 = tl_launches;
+    CUDA_CHECK(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t g = nullptr;
+    try {
+      factor_direct(L, Li, cap_stream_);
+    } catch (...) {
+      cudaStreamEndCapture(cap_stream_, &g);
+      if (g) cudaGraphDestroy(g);
+      tl_launches = l0;
+      throw;
+    }
+    CUDA_CHECK(cudaStreamEndCapture(cap_stream_, &g));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_CHECK(e);
+    it = fgraphs_.emplace(key, FactorGraph{exec, tl_launches - l0}).first;
+    tl_launches = l0;
+  }
+  CUDA_CHECK(cudaGraphLaunch(it->second.exec, st));
+  tl_launches += it->second.launches;
+}
+
+void Engine::compute_inverse(const double* Li, cudaStream_t st) {
+  inverse_from_inverse_factor(Li, ws.ld, ws.np, ws.W, gemm_fn(), st);
   if (cfg_.precision != GLASSO_FP64) refine_inverse(st);
 }
 
 // Mixed mode: Newton-Schulz sweeps W <- W + W R, R = I - A W formed in FP64 from the sparse
-// rows of A; the correction product runs on the tensor cores (its error is |R| times the
-// split-precision error).  Stops once max |R_ij| < 1e-14 (at most three sweeps).
+// rows of A; the correction product runs on the tensor cores, so a sweep leaves a residual of
+// about |R|^2 + 1e-6 |R|.  Sweeps stop once the residual is (or is predicted to be) below
+// 1e-10, which keeps g = S - W, the stop test and the tier-2 log-det difference at FP64-level
+// accuracy for the decisions they feed; at most three sweeps.
 void Engine::refine_inverse(cudaStream_t st) {
   const int np = ws.np;
   const int64_t ld = ws.ld;
   double* rmax = &ws.sc->aux[0];
   for (int sweep = 0; sweep < 3; ++sweep) {
-    inverse_residual(ws.A, ws.W, ld, ws.n, np, ws.X, rmax, st);
+    inverse_residual(ws.A, ws.W, ld, ws.n, np, ws.T, rmax, st);
     double h = 0.0;
     CUDA_CHECK(cudaMemcpyAsync(&h, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
     ws.hs->aux[1 + sweep] = h;
-    if (h < 1e-14) break;
-    GemmArgs g = gemm_args(ws.W, ld, 0, ws.X, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
+    if (h < 1e-10) break;
+    GemmArgs g = gemm_args(ws.W, ld, 0, ws.T, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
     g.lower = 1;
     gemm(g, GemmRole::Refine, st);
     add_lower_mirror(ws.W, ws.Y, ld, np, st);
+    if (h * h + 1e-6 * h < 1e-11) break;  // the sweep just made has brought it below 1e-10
   }
 }
 
@@ -358,15 +428,12 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   }
   // factor the start point
   CUDA_CHECK(cudaMemcpyAsync(ws.Lt, ws.A, mat, cudaMemcpyDeviceToDevice, st));
-  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
-  LAUNCH_CHECK();
-  cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
+  factor(ws.Lt, ws.Lti, st);
   objective_terms(ws.S, ws.A, ld, n, ws.parts, &ws.sc->trsa, st);
-  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
   sync_scalars();
   if (!h.pd_t) throw Error(GLASSO_ERR_NOT_PD, "the start point is not positive definite");
   std::swap(ws.L, ws.Lt);
-  std::swap(ws.Dinv, ws.Dinv_t);
+  std::swap(ws.Li, ws.Lti);
   st_.active = true;
   st_.on_device = s_on_device;
   st_.n = n;
@@ -388,7 +455,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   const double shrink = cfg_.shrink > 0 && cfg_.shrink < 1 ? cfg_.shrink : 0.5;
   const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
 
-  compute_inverse(ws.L, ws.Dinv, st);
+  compute_inverse(ws.Li, st);
   {
     Profiler::Rec rec;
     prof.begin_rec(GLASSO_PROF_GRADIENT, 33.0 * (double)n * (double)n, st, rec);
@@ -417,10 +484,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
             &ws.sc->lin_s, st);
       prof.end_rec(rec, st);
     }
-    k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
-    LAUNCH_CHECK();
-    cholesky_f64(ws.Lt, ld, np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
-    CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    factor(ws.Lt, ws.Lti, st);
     sync_scalars();
     ++trials;
     tier = 1;
@@ -458,7 +522,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   if (!accepted) return GLASSO_LINESEARCH_STALL;
   std::swap(ws.A, ws.At);
   std::swap(ws.L, ws.Lt);
-  std::swap(ws.Dinv, ws.Dinv_t);
+  std::swap(ws.Li, ws.Lti);
   st_.ld_A = h.logdet_t;
   st_.trsa = h.trsa_t;
   st_.l1 = h.l1_t;
@@ -511,10 +575,7 @@ void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double*
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.Lt, false);
   pad_identity(ws.Lt, ws.ld, n, ws.np, st);
-  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
-  LAUNCH_CHECK();
-  cholesky_f64(ws.Lt, ws.ld, ws.np, ws.Dinv_t, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
-  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  factor(ws.Lt, ws.Lti, st);
   k_unpad_lower<<<red_blocks(n), 256, 0, st>>>(ws.Lt, ws.ld, n, L);
   LAUNCH_CHECK();
   sync_scalars();
@@ -529,13 +590,10 @@ int Engine::op_inverse(const double* A, int64_t n, double* W) {
   load_matrix(A, false, true, n, ws.A, false);
   pad_identity(ws.A, ws.ld, n, ws.np, st);
   CUDA_CHECK(cudaMemcpyAsync(ws.L, ws.A, sizeof(double) * ws.ld * ws.np, cudaMemcpyDeviceToDevice, st));
-  k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
-  LAUNCH_CHECK();
-  cholesky_f64(ws.L, ws.ld, ws.np, ws.Dinv, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st);
-  CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  factor(ws.L, ws.Li, st);
   sync_scalars();
   if (!ws.hs->pd_t) return 0;
-  compute_inverse(ws.L, ws.Dinv, st);
+  compute_inverse(ws.Li, st);
   unpad(ws.W, ws.ld, n, W, st);
   CUDA_CHECK(cudaStreamSynchronize(st));
   return 1;

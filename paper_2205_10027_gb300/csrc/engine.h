@@ -2,7 +2,9 @@
 // its line search (Algorithm 1), and the GEMM dispatch by precision mode.
 #pragma once
 #include <chrono>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 #include "../../include/glasso.h"
@@ -18,8 +20,8 @@ struct Workspace {
   int np = 0, cap_np = 0;
   double *S = nullptr, *A = nullptr, *At = nullptr, *W = nullptr, *L = nullptr, *Lt = nullptr;
   double *X = nullptr, *Y = nullptr, *T = nullptr;
+  double *Li = nullptr, *Lti = nullptr;   // L^{-1} of the accepted / trial factor
   int8_t* code = nullptr;                 // np x np
-  double *Dinv = nullptr, *Dinv_t = nullptr;  // np x 64 each
   double* ld_parts = nullptr;             // np / 64
   double* parts = nullptr;                // 8 * kRedBlocks
   Scalars* sc = nullptr;                  // device scalars
@@ -32,6 +34,7 @@ struct Workspace {
   size_t staging_bytes = 0;
   void* tc_scratch = nullptr;             // split operands of the tensor-core GEMMs
   size_t tc_scratch_bytes = 0;
+  uint64_t epoch = 0;                     // bumped at every reallocation
 
   static size_t bytes_for(int np);
   void ensure(int64_t n_new, size_t budget);  // (re)allocate for n_new; throws on failure
@@ -119,10 +122,24 @@ class Engine {
  private:
   void load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst, bool check_s);
   void sandwich(cudaStream_t st);
-  void compute_inverse(const double* L, const double* Dinv, cudaStream_t st);
+  void compute_inverse(const double* Li, cudaStream_t st);
+  void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);
   double power_lambda_max(const double* M, cudaStream_t st);
   void sync_scalars();
+
+  // CUDA graphs of the factorisation, one per (factor buffer, inverse buffer) pair
+  struct FactorGraph {
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  using GraphKey = std::tuple<const double*, const double*, int>;
+  std::map<GraphKey, FactorGraph> fgraphs_;
+  std::map<GraphKey, int> fseen_;
+  uint64_t graph_epoch_ = 0;
+  cudaStream_t cap_stream_ = nullptr;
+  void drop_graphs();
+  void factor_direct(double* L, double* Li, cudaStream_t st);
 
   glasso_config cfg_;
   SolveState st_;

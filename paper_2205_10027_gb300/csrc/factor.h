@@ -10,18 +10,18 @@ namespace glasso {
 enum class GemmRole { Panel, Trailing, Inverse, Sandwich, Refine };
 using GemmFn = std::function<void(const GemmArgs&, GemmRole, cudaStream_t)>;
 
-// In-place lower Cholesky of the np x np matrix A (lower triangle read and overwritten;
-// the upper triangle of the diagonal blocks is zeroed, the rest of the upper triangle is
-// left as it was).  *pd must be 1 on entry and is cleared on a bad pivot, after which the
-// remaining launches do nothing.  *logdet = 2 sum log L_ii (NaN when not PD).
-// Dinv receives the inverses of the 64 x 64 diagonal blocks; ld_parts np/64 doubles.
-void cholesky_f64(double* A, int64_t ld, int np, double* Dinv, double* ld_parts, int* pd,
-                  double* logdet, const GemmFn& gemm, cudaStream_t st);
+// In-place lower Cholesky of the np x np matrix A (lower triangle read and overwritten; the
+// upper triangle of the 64 x 64 diagonal blocks is zeroed, the rest of the upper triangle is
+// left as it was) and X = L^{-1} (lower, written in full).  T is np x np scratch.  *pd must
+// be 1 on entry and is cleared on a bad pivot, after which the remaining launches do nothing;
+// *logdet = 2 sum log L_ii (NaN when not PD).  ld_parts: np/64 doubles.  fp32_leaf: the
+// 64 x 64 leaf blocks are factored and inverted in FP32 arithmetic (split-precision modes).
+void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
+                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf = false);
 
-// W = (L L^T)^{-1} = X^T X with X = L^{-1} built from the factor's lower triangle and the
-// diagonal-block inverses Dinv.  X and T are np x np scratch; W is written in full.
-void inverse_from_factor(const double* L, const double* Dinv, int64_t ld, int np, double* X,
-                         double* T, double* W, const GemmFn& gemm, cudaStream_t st);
+// W = X^T X = (L L^T)^{-1} from X = L^{-1} (lower), written in full.
+void inverse_from_inverse_factor(const double* X, int64_t ld, int np, double* W, const GemmFn& gemm,
+                                 cudaStream_t st);
 
 void mirror_lower(double* M, int64_t ld, int np, cudaStream_t st);
 

@@ -10,7 +10,8 @@ enum KRule : int {
   KR_FULL = 0,    // all of [0, K)
   KR_LO_COL = 1,  // [col0, K): B is lower triangular (B[k][j] = 0 for k < j)
   KR_LO_ROW = 2,  // [row0, K): op(A) is upper triangular (A = X^T with X lower)
-  KR_HI_ROW = 3   // [0, row0 + tile): A is lower triangular (A[i][k] = 0 for k > i)
+  KR_HI_ROW = 3,  // [0, row0 + tile): A is lower triangular (A[i][k] = 0 for k > i)
+  KR_HI_COL = 4   // [0, col0 + tile): op(B) is upper triangular (op(B)[k][j] = 0 for k > j)
 };
 
 // C = alpha op(A) op(B) + beta C.  op(A)[i][k] = transA ? A[k*lda+i] : A[i*lda+k];

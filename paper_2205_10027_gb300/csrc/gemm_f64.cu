@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(THREADS) k_gemm_f64(const __grid_constant__ Ge
   if (p.krule == KR_LO_COL) k_lo = col0;
   else if (p.krule == KR_LO_ROW) k_lo = row0;
   else if (p.krule == KR_HI_ROW) k_hi = min(p.K, row0 + BM);
+  else if (p.krule == KR_HI_COL) k_hi = min(p.K, col0 + BN);
 
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];

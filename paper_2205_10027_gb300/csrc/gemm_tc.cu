@@ -23,6 +23,7 @@ constexpr int TILE_BYTES = 128 * 128;          // 128 rows x 128 bytes of K
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at 2 GHz
+constexpr int GROUP_M = 12;
 
 struct TcArgs {
   double* C;
@@ -127,13 +128,21 @@ __global__ void __launch_bounds__(THREADS, 1)
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               const __grid_constant__ TcArgs p) {
   if (p.flag && *p.flag == 0) return;
-  const int tm = blockIdx.y, tn = blockIdx.x;
+  // grouped tile order: consecutive blocks walk down a column of GROUP_M tiles, so the
+  // CTAs resident at one time cover a near-square patch and share operand panels in L2
+  const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
+  const int per_group = GROUP_M * tiles_n;
+  const int b = blockIdx.x;
+  const int first_m = (b / per_group) * GROUP_M;
+  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int tm = first_m + (b % per_group) % gm, tn = (b % per_group) / gm;
   const int row0 = tm * TM, col0 = tn * TN;
   if (p.lower && row0 + TM <= col0) return;  // tile entirely above the diagonal
   int k_lo = 0, k_hi = p.K;
   if (p.krule == KR_LO_COL) k_lo = col0;
   else if (p.krule == KR_LO_ROW) k_lo = row0;
   else if (p.krule == KR_HI_ROW) k_hi = min(p.K, row0 + TM);
+  else if (p.krule == KR_HI_COL) k_hi = min(p.K, col0 + TN);
   k_lo = (k_lo / p.kstep) * p.kstep;
   const int nk = k_hi > k_lo ? (k_hi - k_lo + p.kstep - 1) / p.kstep : 0;
 
@@ -255,9 +264,10 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(y);
 }
 
+// rows_out >= rows: output rows [rows, rows_out) are written as zeros
 template <bool BF16>
-__global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, int cols, int trans,
-                        void* __restrict__ hi, void* __restrict__ lo, int64_t ldo) {
+__global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, int rows_out, int cols,
+                        int trans, void* __restrict__ hi, void* __restrict__ lo, int64_t ldo) {
   __shared__ double t[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -278,7 +288,7 @@ __global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, i
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int rr = r0 + i, cc = c0 + tx;
-    if (rr >= rows || cc >= cols) continue;
+    if (rr >= rows_out || cc >= cols) continue;
     const double x = t[i][tx];
     const int64_t o = (int64_t)rr * ldo + cc;
     if (BF16) {
@@ -332,13 +342,13 @@ CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld) {
   return m;
 }
 
-void split(const double* src, int64_t lds, int rows, int cols, bool trans, bool bf16, void* hi, void* lo,
-           int64_t ldo, cudaStream_t st) {
-  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+void split(const double* src, int64_t lds, int rows, int rows_out, int cols, bool trans, bool bf16,
+           void* hi, void* lo, int64_t ldo, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows_out + 31) / 32);
   if (bf16)
-    k_split<true><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, trans, hi, lo, ldo);
+    k_split<true><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, rows_out, cols, trans, hi, lo, ldo);
   else
-    k_split<false><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, trans, hi, lo, ldo);
+    k_split<false><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, rows_out, cols, trans, hi, lo, ldo);
   LAUNCH_CHECK();
 }
 
@@ -350,8 +360,7 @@ bool tc_available() { return encode_fn() != nullptr; }
 size_t tc_scratch_bytes_for(int np) { return (size_t)4 * np * np * sizeof(float) + 256; }
 
 bool tc_gemm_supported(const GemmArgs& a) {
-  // 128-row tiles; smaller products stay on the FP64 kernel
-  return a.M % 64 == 0 && a.N % 64 == 0 && a.K % 64 == 0 && a.M >= 128 && a.N >= 128 && a.K >= 64;
+  return a.M % 64 == 0 && a.N % 64 == 0 && a.K % 64 == 0 && a.M > 0 && a.N > 0 && a.K > 0;
 }
 
 int tc_error_flag(cudaStream_t st) {
@@ -365,7 +374,8 @@ int tc_error_flag(cudaStream_t st) {
 void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st) {
   const bool bf16 = kind == TcKind::BF16x3;
   const size_t esz = bf16 ? 2 : 4;
-  const size_t need = esz * ((size_t)2 * a.M * a.K + (size_t)2 * a.N * a.K);
+  const size_t need = esz * ((size_t)2 * ((a.M + TM - 1) / TM * TM) * a.K +
+                             (size_t)2 * ((a.N + TN - 1) / TN * TN) * a.K);
   if (need + 256 > scratch_bytes) throw Error(GLASSO_ERR_OOM, "tensor-core scratch too small");
   static std::once_flag once;
   std::call_once(once, [] {
@@ -373,16 +383,19 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
     CUDA_CHECK(cudaMemset(g_err, 0, sizeof(int)));
     CUDA_CHECK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   });
+  // split operands are stored with their row counts rounded up to the 128-row tile (zero
+  // rows beyond M or N), so every TMA box lies inside its tensor
+  const int Mp = (a.M + TM - 1) / TM * TM, Np = (a.N + TN - 1) / TN * TN;
   uint8_t* base = static_cast<uint8_t*>(scratch);
   void* Ah = base;
-  void* Al = base + esz * (size_t)a.M * a.K;
-  void* Bh = base + esz * (size_t)2 * a.M * a.K;
-  void* Bl = base + esz * ((size_t)2 * a.M * a.K + (size_t)a.N * a.K);
+  void* Al = base + esz * (size_t)Mp * a.K;
+  void* Bh = base + esz * (size_t)2 * Mp * a.K;
+  void* Bl = base + esz * ((size_t)2 * Mp * a.K + (size_t)Np * a.K);
   // A part: [M][K] = op(A); B part: [N][K] = op(B)^T
-  split(a.A, a.lda, a.M, a.K, a.transA != 0, bf16, Ah, Al, a.K, st);
-  split(a.B, a.ldb, a.N, a.K, a.transB == 0, bf16, Bh, Bl, a.K, st);
-  const CUtensorMap mAh = make_map(Ah, bf16, a.M, a.K, a.K), mAl = make_map(Al, bf16, a.M, a.K, a.K);
-  const CUtensorMap mBh = make_map(Bh, bf16, a.N, a.K, a.K), mBl = make_map(Bl, bf16, a.N, a.K, a.K);
+  split(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, bf16, Ah, Al, a.K, st);
+  split(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, bf16, Bh, Bl, a.K, st);
+  const CUtensorMap mAh = make_map(Ah, bf16, Mp, a.K, a.K), mAl = make_map(Al, bf16, Mp, a.K, a.K);
+  const CUtensorMap mBh = make_map(Bh, bf16, Np, a.K, a.K), mBl = make_map(Bl, bf16, Np, a.K, a.K);
   TcArgs p;
   p.C = a.C;
   p.ldc = a.ldc;
@@ -398,7 +411,7 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
   p.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   p.flag = a.flag;
   p.err = g_err;
-  dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM);
+  dim3 grid(((a.N + TN - 1) / TN) * ((a.M + TM - 1) / TM));
   k_gemm_tc<<<grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
   LAUNCH_CHECK();
 }
