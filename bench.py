@@ -254,6 +254,10 @@ def run_ours(args):
               "frac": achieved / peak if peak else None, "traffic": None,
               "peak_source": peak_kind if args.precision == "fp64" else f"{peak_kind} bf16 sustained x nominal dtype ratio / 3 split products",
               "launches": g_launch, "share_of_step": g_ms / ms if ms else None}
+        if "factor" in prof and prof["factor"]["ms"]:
+            # the factorisations replay as CUDA graphs: timed as whole graphs (2 n^3 / 3 FLOPs)
+            rl["factor_graph"] = {"ms": prof["factor"]["ms"], "launches": prof["factor"]["launches"],
+                                  "tflops": prof["factor"]["work"] / (prof["factor"]["ms"] / 1e3) / 1e12}
         hbm = {}
         for c in ("gradient", "trial"):
             if c in prof and prof[c]["ms"]:

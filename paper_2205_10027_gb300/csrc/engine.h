@@ -140,6 +140,7 @@ class Engine {
   cudaStream_t cap_stream_ = nullptr;
   void drop_graphs();
   void factor_direct(double* L, double* Li, cudaStream_t st);
+  void factor_graphed(double* L, double* Li, cudaStream_t st);
 
   glasso_config cfg_;
   SolveState st_;

@@ -258,13 +258,49 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---- operand splitting: out[r][c] = op[r][c], op = src or its transpose, into hi + lo parts
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return __uint_as_float(y);
+// hi = x rounded to SIG significant bits (nearest, ties away), lo = (x - hi) rounded the same
+// way, returned as FP32 bit patterns (the low 24 - SIG mantissa bits zero).  Integer
+// arithmetic only: the FP64 pipe of this part is too narrow to convert at memory speed.
+// Magnitudes outside the FP32 normal range become 0 (hi) or are dropped (lo).
+template <int SIG>
+__device__ __forceinline__ void split_bits(double x, uint32_t& hi, uint32_t& lo) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF);
+  hi = 0;
+  lo = 0;
+  if (e == 0 || e == 0x7FF) return;
+  const uint64_t M = (1ull << 52) | (b & ((1ull << 52) - 1));
+  constexpr int SH = 53 - SIG;
+  uint64_t Mh = (M + (1ull << (SH - 1))) >> SH;
+  const int64_t rem = (int64_t)M - (int64_t)(Mh << SH);
+  int fe = e - 1023 + 127;
+  if (Mh >> SIG) {
+    Mh >>= 1;
+    fe += 1;
+  }
+  if (fe <= 0 || fe >= 255) return;
+  hi = sign | ((uint32_t)fe << 23) | ((uint32_t)(Mh & ((1u << (SIG - 1)) - 1)) << (24 - SIG));
+  if (rem == 0) return;
+  uint64_t r = rem < 0 ? (uint64_t)(-rem) : (uint64_t)rem;
+  const uint32_t slo = (((uint32_t)(b >> 63)) ^ (rem < 0 ? 1u : 0u)) << 31;
+  int top = 63 - __clzll((long long)r);
+  uint64_t rr;
+  if (top >= SIG) {
+    const int s2 = top - (SIG - 1);
+    rr = (r + (1ull << (s2 - 1))) >> s2;
+    if (rr >> SIG) {
+      rr >>= 1;
+      top += 1;
+    }
+  } else {
+    rr = r << ((SIG - 1) - top);
+  }
+  const int fe_lo = top + e - 1075 + 127;
+  if (fe_lo <= 0 || fe_lo >= 255) return;
+  lo = slo | ((uint32_t)fe_lo << 23) | ((uint32_t)(rr & ((1u << (SIG - 1)) - 1)) << (24 - SIG));
 }
 
-// rows_out >= rows: output rows [rows, rows_out) are written as zeros
 template <bool BF16>
 __global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, int rows_out, int cols,
                         int trans, void* __restrict__ hi, void* __restrict__ lo, int64_t ldo) {
@@ -291,16 +327,15 @@ __global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, i
     if (rr >= rows_out || cc >= cols) continue;
     const double x = t[i][tx];
     const int64_t o = (int64_t)rr * ldo + cc;
+    uint32_t h, l;
     if (BF16) {
-      const __nv_bfloat16 h = __double2bfloat16(x);
-      const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
-      reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
-      reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+      split_bits<8>(x, h, l);
+      reinterpret_cast<uint16_t*>(hi)[o] = (uint16_t)(h >> 16);
+      reinterpret_cast<uint16_t*>(lo)[o] = (uint16_t)(l >> 16);
     } else {
-      const float h = tf32_round((float)x);
-      const float l = tf32_round((float)(x - (double)h));
-      reinterpret_cast<float*>(hi)[o] = h;
-      reinterpret_cast<float*>(lo)[o] = l;
+      split_bits<11>(x, h, l);
+      reinterpret_cast<uint32_t*>(hi)[o] = h;
+      reinterpret_cast<uint32_t*>(lo)[o] = l;
     }
   }
 }

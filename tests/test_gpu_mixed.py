@@ -5,8 +5,8 @@ Stated tolerances (relative Frobenius unless noted), derived from the split arit
 hi + lo carries 22 (TF32) or 16 (BF16) significant bits, the dropped lo*lo term and the FP32
 accumulation over K add about 2^-24 sqrt(K):
   sandwich Y = A X A        TF32x3 <= 2e-5, BF16x3 <= 1e-4
-  Cholesky factor           TF32x3 <= 1e-6, BF16x3 <= 1e-5;  log det within 1e-7 |log det|
-                            (TF32x3) or 1e-6 |log det| (BF16x3)
+  Cholesky factor           TF32x3 <= 1e-6, BF16x3 <= 1e-5;  log det within 1e-6 |log det|
+                            (the 64 x 64 leaves run in FP32)
   W after FP64 refinement   <= 1e-9 (sweeps stop once max|I - A W| < 1e-10; the residual is
                             formed in FP64)
   whole solve at tol        KKT residual (host, FP64) <= 1.05 tol, iterations within 3 of
@@ -22,7 +22,7 @@ from paper_2205_10027_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32x3": dict(sandwich=2e-5, chol=1e-6, logdet=1e-7),
+TOL = {"tf32x3": dict(sandwich=2e-5, chol=1e-6, logdet=1e-6),
        "bf16x3": dict(sandwich=1e-4, chol=1e-5, logdet=1e-6)}
 
 

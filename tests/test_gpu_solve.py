@@ -196,5 +196,7 @@ def test_profile_accounts_kernel_classes(fp64):
     fp64.profile_start()
     fp64.solve(p.S, p.lam, 1e-6)
     prof = fp64.profile_stop()
-    for cls in ("sandwich", "trailing", "inverse", "gradient", "trial"):
+    for cls in ("sandwich", "inverse", "gradient", "trial"):
         assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
+    # factorisations run launch by launch until their CUDA graph exists, then as one replay
+    assert prof["trailing"]["launches"] > 0 and prof["factor"]["launches"] > 0
