@@ -63,6 +63,40 @@ __device__ __forceinline__ double soft_threshold(double v, double c) {
   return m > 0.0 ? copysign(m, v) : 0.0;
 }
 
+// Conversions between FP64 and FP32 by integer arithmetic (the FP64 pipe of this part is too
+// narrow for bulk conversions).  Zero and subnormal inputs give zero; values beyond the FP32
+// range are not expected by the callers (factor blocks of SPD matrices) and saturate to the
+// largest finite magnitude; Inf and NaN become NaN, so a PD test downstream still fails.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFF;
+  if (e == 0) return 0.0;
+  const uint64_t s = (uint64_t)(u >> 31) << 63;
+  const uint64_t m = (uint64_t)(u & 0x7FFFFF) << 29;
+  const uint64_t e64 = (e == 0xFF) ? 0x7FF : (uint64_t)(e - 127 + 1023);
+  return __longlong_as_double((long long)(s | (e64 << 52) | m));
+}
+__device__ __forceinline__ float f64_to_f32(double d) {  // round to nearest even
+  const uint64_t b = (uint64_t)__double_as_longlong(d);
+  const uint32_t s = (uint32_t)(b >> 63) << 31;
+  if (((b >> 52) & 0x7FF) == 0x7FF) return __uint_as_float(0x7FC00000u);  // Inf / NaN -> NaN
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(s);
+  uint64_t m = b & ((1ull << 52) - 1);
+  uint32_t m23 = (uint32_t)(m >> 29);
+  const uint64_t rem = m & ((1ull << 29) - 1);
+  uint32_t bits = ((uint32_t)e << 23) + m23;
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (m23 & 1u))) ++bits;  // carries into e
+  if (e >= 0xFF || bits >= 0x7F800000u) bits = 0x7F7FFFFFu;
+  return __uint_as_float(s | bits);
+}
+
+template <typename T> __device__ __forceinline__ T from_f64(double d);
+template <> __device__ __forceinline__ double from_f64<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return f64_to_f32(d); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+
 }  // namespace glasso
 
 #include <stdexcept>

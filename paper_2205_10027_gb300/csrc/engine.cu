@@ -1,6 +1,7 @@
 // pISTA outer loop (Algorithm 1) on the device kernels, with the line search of
 // Sec. 4.3.2 and the Sec. 6 fallback step, and the single-step operations of the C ABI.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include "engine.h"
 #include "gemm_tc.h"
@@ -203,6 +204,15 @@ int prof_class(GemmRole r) {
 // ------------------------------------------------------------------------------------------
 Engine::Engine(const glasso_config& cfg) : cfg_(cfg) {
   CUDA_CHECK(cudaSetDevice(cfg.device));
+  // GLASSO_NO_GRAPHS=1 runs every factorisation launch by launch (for per-kernel profiling)
+  const char* ng = std::getenv("GLASSO_NO_GRAPHS");
+  use_graphs_ = !(ng && ng[0] == '1');
+  // width of the right-looking panels of the factorisation (GLASSO_PANEL overrides; 0, the
+  // default, = recursive halving over the whole matrix, which measured faster on GB300:
+  // its trailing updates have K up to n/2 instead of the panel width)
+  const char* pw = std::getenv("GLASSO_PANEL");
+  panel_ = pw ? std::atoi(pw) : 0;
+  if (panel_ < 0 || panel_ % kPad) panel_ = 0;
   ws.device = cfg.device;
   if (cfg.stream) {
     stream_ = (cudaStream_t)cfg.stream;
@@ -229,6 +239,8 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
     tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
             ws.tc_scratch, ws.tc_scratch_bytes, st);
   } else {
+    // the FP64 kernel reads its operands tile by tile while writing C: no aliasing allowed
+    if (a.C == a.A || a.C == a.B) throw Error(GLASSO_ERR_ARG, "in-place product on the FP64 kernel");
     gemm_f64(a, 1, st);
   }
   prof.end_rec(rec, st);
@@ -288,7 +300,7 @@ void Engine::factor_direct(double* L, double* Li, cudaStream_t st) {
   k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
   LAUNCH_CHECK();
   cholesky_inverse(L, Li, ws.ld, ws.np, ws.T, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st,
-                   cfg_.precision != GLASSO_FP64);
+                   cfg_.precision != GLASSO_FP64, panel_);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
 }
 
@@ -310,6 +322,12 @@ void Engine::factor(double* L, double* Li, cudaStream_t st) {
   if (graph_epoch_ != ws.epoch) {
     drop_graphs();
     graph_epoch_ = ws.epoch;
+  }
+  if (!use_graphs_) {
+    prof.begin_rec(GLASSO_PROF_FACTOR, 2.0 * np3 / 3.0, st, rec);
+    factor_direct(L, Li, st);
+    prof.end_rec(rec, st);
+    return;
   }
   const bool graphed = fgraphs_.count(GraphKey{L, Li, ws.np}) != 0;
   if (graphed) prof.begin_rec(GLASSO_PROF_FACTOR, 2.0 * np3 / 3.0, st, rec);
@@ -357,7 +375,10 @@ void Engine::factor_graphed(double* L, double* Li, cudaStream_t st) {
   tl_launches += it->second.launches;
 }
 
-void Engine::compute_inverse(const double* Li, cudaStream_t st) {
+// W = A^{-1} for the accepted factor (ws.L, Li): completes Li = L^{-1} from its diagonal panel
+// blocks, then W = Li^T Li.
+void Engine::compute_inverse(double* Li, cudaStream_t st) {
+  if (panel_ > 0) inverse_merge(ws.L, Li, ws.ld, ws.np, ws.T, panel_, gemm_fn(), st);
   inverse_from_inverse_factor(Li, ws.ld, ws.np, ws.W, gemm_fn(), st);
   if (cfg_.precision != GLASSO_FP64) refine_inverse(st);
 }

@@ -122,7 +122,7 @@ class Engine {
  private:
   void load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst, bool check_s);
   void sandwich(cudaStream_t st);
-  void compute_inverse(const double* Li, cudaStream_t st);
+  void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);
   double power_lambda_max(const double* M, cudaStream_t st);
@@ -137,6 +137,8 @@ class Engine {
   std::map<GraphKey, FactorGraph> fgraphs_;
   std::map<GraphKey, int> fseen_;
   uint64_t graph_epoch_ = 0;
+  bool use_graphs_ = true;
+  int panel_ = 0;
   cudaStream_t cap_stream_ = nullptr;
   void drop_graphs();
   void factor_direct(double* L, double* Li, cudaStream_t st);

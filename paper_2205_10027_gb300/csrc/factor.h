@@ -11,13 +11,22 @@ enum class GemmRole { Panel, Trailing, Inverse, Sandwich, Refine };
 using GemmFn = std::function<void(const GemmArgs&, GemmRole, cudaStream_t)>;
 
 // In-place lower Cholesky of the np x np matrix A (lower triangle read and overwritten; the
-// upper triangle of the 64 x 64 diagonal blocks is zeroed, the rest of the upper triangle is
-// left as it was) and X = L^{-1} (lower, written in full).  T is np x np scratch.  *pd must
-// be 1 on entry and is cleared on a bad pivot, after which the remaining launches do nothing;
-// *logdet = 2 sum log L_ii (NaN when not PD).  ld_parts: np/64 doubles.  fp32_leaf: the
-// 64 x 64 leaf blocks are factored and inverted in FP32 arithmetic (split-precision modes).
+// upper triangle of the leaf blocks is zeroed, the rest of the upper triangle is left as it
+// was).  panel <= 0: recursive halving over the whole matrix, and X = L^{-1} is written in full.
+// panel > 0: right-looking over panels of that width (a multiple of the leaf), each diagonal
+// block factored recursively; X then holds only the inverses of the diagonal panel blocks
+// (inverse_merge completes it).  T is np x np scratch.  *pd must be 1 on entry and is
+// cleared on a bad pivot, after which the remaining launches do nothing; *logdet =
+// 2 sum log L_ii (NaN when not PD).  ld_parts: np/64 doubles.  fp32_leaf: the leaf blocks are
+// factored and inverted in FP32 arithmetic (split-precision modes).
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
-                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf = false);
+                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf = false,
+                      int panel = 0);
+
+// Completes X = L^{-1} from the inverses of the diagonal panel blocks left by
+// cholesky_inverse(..., panel).  T is np x np scratch.
+void inverse_merge(const double* L, double* X, int64_t ld, int np, double* T, int panel, const GemmFn& gemm,
+                   cudaStream_t st);
 
 // W = X^T X = (L L^T)^{-1} from X = L^{-1} (lower), written in full.
 void inverse_from_inverse_factor(const double* X, int64_t ld, int np, double* W, const GemmFn& gemm,

@@ -2,13 +2,14 @@
 //
 // Each FP64 operand is split into hi + lo parts of a narrow type (TF32 or BF16); the product
 // op(A) op(B) is formed as hi*hi + hi*lo + lo*hi by tcgen05.mma with FP32 accumulation in
-// TMEM, and the epilogue adds alpha * acc to beta * C in FP64.  One CTA computes a
+// TMEM, and the epilogue writes alpha * acc + beta * C (FP32 arithmetic, FP64 storage).  One CTA computes a
 // 128 x 128 output tile: one thread issues TMA loads of the four 128 x (128 bytes) operand
 // tiles of a k-stage into a 3-stage shared-memory ring (128-byte swizzle), one thread issues
 // the MMAs, and all four warps drain the accumulator with tcgen05.ld.  Every wait on an
 // mbarrier is bounded; on a timeout the CTA records an error and leaves without writing.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include "engine.h"
 #include "gemm_tc.h"
 
@@ -240,13 +241,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
       }
       if (r < p.M) {
+        // FP32 arithmetic with integer conversions (the FP64 pipe is too narrow to spend two
+        // operations per output element); C stays FP64 in memory.  alpha and beta are 0 or
+        // +-1 in every product of the solver, so only the beta != 0 update rounds, to FP32,
+        // which is the accuracy of the split products themselves.
         double* dst = p.C + (int64_t)r * p.ldc + col0 + c * 32;
+        const float al = (float)p.alpha, be = (float)p.beta;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = col0 + c * 32 + j;
           if (col >= p.N || (p.lower && col > r)) continue;
-          const double a = p.alpha * (double)v[j];
-          dst[j] = (p.beta == 0.0) ? a : fma(p.beta, dst[j], a);
+          const float a = al * v[j];
+          dst[j] = f32_to_f64(p.beta == 0.0 ? a : fmaf(be, f64_to_f32(dst[j]), a));
         }
       }
     }
@@ -301,41 +307,56 @@ __device__ __forceinline__ void split_bits(double x, uint32_t& hi, uint32_t& lo)
   lo = slo | ((uint32_t)fe_lo << 23) | ((uint32_t)(rr & ((1u << (SIG - 1)) - 1)) << (24 - SIG));
 }
 
+// One split job: out[r][c] = op[r][c] for r < rows_out (zero rows at and beyond `rows`).
+struct SplitJob {
+  const double* src;
+  int64_t lds;
+  int rows, rows_out, cols, trans;
+  void* hi;
+  void* lo;
+  int64_t ldo;
+  int tiles_x;  // 32-column tiles of the output
+};
+
+// blockIdx.z selects the job: the A and B operands of a product are split in one launch.
 template <bool BF16>
-__global__ void k_split(const double* __restrict__ src, int64_t lds, int rows, int rows_out, int cols,
-                        int trans, void* __restrict__ hi, void* __restrict__ lo, int64_t ldo) {
+__global__ void k_split(const __grid_constant__ SplitJob ja, const __grid_constant__ SplitJob jb) {
+  const SplitJob& j = blockIdx.z == 0 ? ja : jb;
+  const int tiles_y = (j.rows_out + 31) / 32;
+  if ((int)blockIdx.x >= j.tiles_x || (int)blockIdx.y >= tiles_y) return;
   __shared__ double t[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const double* __restrict__ src = j.src;
   for (int i = ty; i < 32; i += 8) {
     // load the (r0, c0) tile of op: element (r0 + i, c0 + tx) of op
     double v = 0.0;
-    if (!trans) {
+    if (!j.trans) {
       const int rr = r0 + i, cc = c0 + tx;
-      if (rr < rows && cc < cols) v = src[(int64_t)rr * lds + cc];
+      if (rr < j.rows && cc < j.cols) v = src[(int64_t)rr * j.lds + cc];
       t[i][tx] = v;
     } else {
       // op[r][c] = src[c][r]: read src row c0 + i, columns r0 + tx (coalesced)
       const int sr = c0 + i, sc = r0 + tx;
-      if (sr < cols && sc < rows) v = src[(int64_t)sr * lds + sc];
+      if (sr < j.cols && sc < j.rows) v = src[(int64_t)sr * j.lds + sc];
       t[tx][i] = v;
     }
   }
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int rr = r0 + i, cc = c0 + tx;
-    if (rr >= rows_out || cc >= cols) continue;
+    if (rr >= j.rows_out || cc >= j.cols) continue;
     const double x = t[i][tx];
-    const int64_t o = (int64_t)rr * ldo + cc;
+    const int64_t o = (int64_t)rr * j.ldo + cc;
     uint32_t h, l;
     if (BF16) {
       split_bits<8>(x, h, l);
-      reinterpret_cast<uint16_t*>(hi)[o] = (uint16_t)(h >> 16);
-      reinterpret_cast<uint16_t*>(lo)[o] = (uint16_t)(l >> 16);
+      reinterpret_cast<uint16_t*>(j.hi)[o] = (uint16_t)(h >> 16);
+      reinterpret_cast<uint16_t*>(j.lo)[o] = (uint16_t)(l >> 16);
     } else {
       split_bits<11>(x, h, l);
-      reinterpret_cast<uint32_t*>(hi)[o] = h;
-      reinterpret_cast<uint32_t*>(lo)[o] = l;
+      reinterpret_cast<uint32_t*>(j.hi)[o] = h;
+      reinterpret_cast<uint32_t*>(j.lo)[o] = l;
     }
   }
 }
@@ -377,13 +398,17 @@ CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld) {
   return m;
 }
 
-void split(const double* src, int64_t lds, int rows, int rows_out, int cols, bool trans, bool bf16,
-           void* hi, void* lo, int64_t ldo, cudaStream_t st) {
-  dim3 grid((cols + 31) / 32, (rows_out + 31) / 32);
+SplitJob split_job(const double* src, int64_t lds, int rows, int rows_out, int cols, bool trans, void* hi,
+                   void* lo, int64_t ldo) {
+  return SplitJob{src, lds, rows, rows_out, cols, trans ? 1 : 0, hi, lo, ldo, (cols + 31) / 32};
+}
+
+void split2(const SplitJob& a, const SplitJob& b, bool bf16, cudaStream_t st) {
+  dim3 grid(std::max(a.tiles_x, b.tiles_x), (std::max(a.rows_out, b.rows_out) + 31) / 32, 2);
   if (bf16)
-    k_split<true><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, rows_out, cols, trans, hi, lo, ldo);
+    k_split<true><<<grid, dim3(32, 8), 0, st>>>(a, b);
   else
-    k_split<false><<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, rows_out, cols, trans, hi, lo, ldo);
+    k_split<false><<<grid, dim3(32, 8), 0, st>>>(a, b);
   LAUNCH_CHECK();
 }
 
@@ -427,8 +452,8 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
   void* Bh = base + esz * (size_t)2 * Mp * a.K;
   void* Bl = base + esz * ((size_t)2 * Mp * a.K + (size_t)Np * a.K);
   // A part: [M][K] = op(A); B part: [N][K] = op(B)^T
-  split(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, bf16, Ah, Al, a.K, st);
-  split(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, bf16, Bh, Bl, a.K, st);
+  split2(split_job(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, Ah, Al, a.K),
+         split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K), bf16, st);
   const CUtensorMap mAh = make_map(Ah, bf16, Mp, a.K, a.K), mAl = make_map(Al, bf16, Mp, a.K, a.K);
   const CUtensorMap mBh = make_map(Bh, bf16, Np, a.K, a.K), mBl = make_map(Bl, bf16, Np, a.K, a.K);
   TcArgs p;

@@ -13,7 +13,8 @@ size_t tc_scratch_bytes_for(int np);
 // Whether the tensor-core kernel covers this product's shape and options.
 bool tc_gemm_supported(const GemmArgs& a);
 // C = alpha op(A) op(B) + beta C with each FP64 operand split into hi + lo parts and the
-// three products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, then added to C in FP64.
+// three products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM; the epilogue combines
+// with beta * C in FP32 arithmetic and stores FP64.
 void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st);
 // Whether the driver exposes what the tensor-core path needs (TMA descriptor encoding).
 bool tc_available();

@@ -191,11 +191,12 @@ def test_stepwise_equals_solve(fp64, glasso):
     assert res["kernel_launches"] > 0
 
 
-def test_profile_accounts_kernel_classes(fp64):
+def test_profile_accounts_kernel_classes(glasso):
     p = inputs.grid_n10000(side=12, m=30)
-    fp64.profile_start()
-    fp64.solve(p.S, p.lam, 1e-6)
-    prof = fp64.profile_stop()
+    with glasso.Handle(precision="fp64") as h:   # fresh: no factorisation graph captured yet
+        h.profile_start()
+        h.solve(p.S, p.lam, 1e-6)
+        prof = h.profile_stop()
     for cls in ("sandwich", "inverse", "gradient", "trial"):
         assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
     # factorisations run launch by launch until their CUDA graph exists, then as one replay
