@@ -5,8 +5,13 @@ cached factor, gradient / free set / sign guess / stop test, the sandwich produc
 and the line search with a Cholesky factorisation per trial), on a 100 x 100 lattice
 precision (4-neighbour weights -1, diagonal 4.1), m = 2,000 samples, lambda = 0.1.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3|bf16x3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32x3|fp64]
+                  [--products auto|dense|sparse]
   python bench.py --impl reference ...   the FP64 CPU oracle on a bounded sample
+
+The default line is the BF16x3 split-precision form with the automatic choice of sandwich
+products; it also reports the time to relative KKT residual 1e-6 and the plain FP64 form's
+iterations/s and time to the same tolerance on the same workload.
 
 For N > 1 (torchrun) every rank solves its own replica (the single solve does not shard):
 value = the iterations of all ranks / the slowest rank's time.  Prints one JSON line.
@@ -174,7 +179,8 @@ def run_ours(args):
     n = p.S.shape[0]
     S_dev = torch.from_numpy(np.ascontiguousarray(p.S)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream)
+    h = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
+                       products=args.products)
 
     def barrier():
         if world > 1:
@@ -209,7 +215,7 @@ def run_ours(args):
     S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
     out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
     he = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
-                        max_iter=args.steps)
+                        max_iter=args.steps, products=args.products)
     he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())  # warm the workspace
     barrier()
     t0 = time.perf_counter()
@@ -222,7 +228,8 @@ def run_ours(args):
     # ---- time to tolerance (device-resident) ---------------------------------------------------
     ttt = None
     if args.time_to_tol:
-        ht = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream, max_iter=2000)
+        ht = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream, max_iter=2000,
+                            products=args.products)
         barrier()
         t0 = time.perf_counter()
         _, rt = ht.solve(S_dev, p.lam, p.tol)
@@ -230,6 +237,31 @@ def run_ours(args):
         ttt = {"seconds": time.perf_counter() - t0, "iterations": rt["iterations"], "trials": rt["trials"],
                "rel_kkt_l1": rt["rel_kkt_l1"], "status": binding.STATUS[rt["status"]]}
         ht.close()
+
+    # ---- the plain FP64 form on the same workload (what the split-precision form must beat) --
+    fp64 = None
+    if args.fp64_form and args.precision != "fp64":
+        hf = binding.Handle(precision="fp64", device=local, stream=stream.cuda_stream, max_iter=2000,
+                            products=args.products)
+        hf.begin(S_dev, p.lam)
+        hf.step(0.0)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(2):
+            hf.step(0.0)
+        f1.record(stream)
+        barrier()
+        hf.end()
+        fp64 = {"iters_per_s": job_throughput(2, world, max_over_ranks(f0.elapsed_time(f1)) / 1000.0)}
+        if args.time_to_tol:
+            barrier()
+            t0 = time.perf_counter()
+            _, rf = hf.solve(S_dev, p.lam, p.tol)
+            barrier()
+            fp64.update({"time_to_tol_s": time.perf_counter() - t0, "iterations": rf["iterations"],
+                         "rel_kkt_l1": rf["rel_kkt_l1"], "status": binding.STATUS[rf["status"]]})
+        hf.close()
     h.close()
 
     if rank == 0:
@@ -277,7 +309,8 @@ def run_ours(args):
             "dtype": {"fp64": "f64", "tf32x3": "f64+tf32x3", "bf16x3": "f64+bf16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"grid{args.side}x{args.side}_n{n}_m{args.m}_lam0.1",
-                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "precision": args.precision, "products": args.products,
+                       "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (each n x n FP64 matrix is %.0f MB)" % (8 * n * n / 1e6)},
             "gpu_launches": launches, "trials_in_timed_steps": trials,
             "last_step": {"rel_kkt_l1": last["rel_kkt_l1"], "iterations": last["iterations"]},
@@ -288,6 +321,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "time_to_tol": ttt,
+            "fp64_form": fp64,
         }
         print(json.dumps(line))
     if world > 1:
@@ -307,7 +341,7 @@ def run_op(args):
     X = 0.5 * (X + X.T)
     Ad, Xd = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
     Sd = torch.from_numpy(p.S + np.eye(n)).cuda()
-    h = binding.Handle(precision=args.precision)
+    h = binding.Handle(precision=args.precision, products=args.products)
     fn = (lambda: h.op_sandwich(Ad, Xd)) if args.op == "sandwich" else (lambda: h.op_cholesky(Sd))
     for _ in range(args.warmup):
         fn()
@@ -459,11 +493,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="bf16x3")
+    ap.add_argument("--products", choices=["auto", "dense", "sparse"], default="auto",
+                    help="how the sandwich products are formed (glasso_products)")
     ap.add_argument("--side", type=int, default=100)
     ap.add_argument("--m", type=int, default=2000)
     ap.add_argument("--sample-side", type=int, default=50)
-    ap.add_argument("--time-to-tol", action="store_true")
+    ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false",
+                    help="skip the time-to-tolerance solve")
+    ap.add_argument("--time-to-tol", dest="time_to_tol", action="store_true")
+    ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false",
+                    help="skip the plain FP64 form's iterations/s and time-to-tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--op", choices=["sandwich", "cholesky"], default=None,
                     help="micro-benchmark one kernel class instead of the step")

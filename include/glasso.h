@@ -57,6 +57,13 @@ typedef enum {
 typedef enum { GLASSO_F64 = 0, GLASSO_F32 = 1 } glasso_dtype;
 typedef enum { GLASSO_HOST = 0, GLASSO_DEVICE = 1 } glasso_memory;
 
+/* How Theta X Theta (eq. b) is formed.  DENSE: two dense products (tensor cores in the
+ * split-precision modes, FP64 CUDA cores otherwise).  SPARSE: two FP64 products with Theta in
+ * CSR form, O(nnz(Theta) n) work, exact to FP64 rounding; used while nnz(Theta) <= 256 n.
+ * AUTO (default): SPARSE in the FP64 form, and in the split-precision forms while
+ * nnz(Theta) <= n max(16, n / 256), where it also costs less than the dense products. */
+typedef enum { GLASSO_PRODUCTS_AUTO = 0, GLASSO_PRODUCTS_DENSE = 1, GLASSO_PRODUCTS_SPARSE = 2 } glasso_products;
+
 typedef struct glasso_handle glasso_handle;
 
 typedef struct {
@@ -68,6 +75,7 @@ typedef struct {
   double t_min;             /* halving stops below this t; default 1e-4 (Sec. 6) */
   size_t hbm_budget_bytes;  /* device memory the handle may hold; 0 = no limit */
   int serve_slots;          /* requests the serving loop runs at once; default 8 */
+  int products;             /* glasso_products: how the sandwich products of eq. b are formed */
 } glasso_config;
 
 typedef struct {
@@ -149,7 +157,14 @@ enum {
   GLASSO_PROF_TRIAL = 6,      /* trial-point pass: bytes moved */
   GLASSO_PROF_FACTOR = 7,     /* whole Cholesky-with-inverse calls (their products included):
                                  FLOPs n^3/3 + n^3/3 */
-  GLASSO_PROF_CLASSES = 8
+  GLASSO_PROF_RESIDUAL = 8,   /* mixed mode: FP64 residual I - Theta W from the sparse rows of
+                                 Theta: bytes of the Theta read and the residual write */
+  GLASSO_PROF_LOGDET2 = 9,    /* second-order log-det difference near the decision boundary:
+                                 bytes of the dTheta W and trace passes */
+  GLASSO_PROF_AUX = 10,       /* symmetrising copies of W and the refinement update: bytes */
+  GLASSO_PROF_SPMM = 11,      /* sparse sandwich products with their CSR build: FP64 FLOPs
+                                 2 nnz(Theta) n + nnz(Theta) n (the second product lower only) */
+  GLASSO_PROF_CLASSES = 12
 };
 
 typedef struct {

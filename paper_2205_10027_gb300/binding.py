@@ -32,7 +32,7 @@ HOST, DEVICE = 0, 1
 class glasso_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("precision", C.c_int),
                 ("max_iter", C.c_int), ("shrink", C.c_double), ("t_min", C.c_double),
-                ("hbm_budget_bytes", C.c_size_t), ("serve_slots", C.c_int)]
+                ("hbm_budget_bytes", C.c_size_t), ("serve_slots", C.c_int), ("products", C.c_int)]
 
 
 class glasso_result(C.Structure):
@@ -46,11 +46,13 @@ class glasso_result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PROF_CLASSES = ("sandwich", "trailing", "panel", "inverse", "refine", "gradient", "trial", "factor")
+PROF_CLASSES = ("sandwich", "trailing", "panel", "inverse", "refine", "gradient", "trial", "factor",
+                "residual", "logdet2", "aux", "spmm")
 
 
 class glasso_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("work", C.c_double * 8), ("launches", C.c_int64 * 8)]
+    _fields_ = [("ms", C.c_double * len(PROF_CLASSES)), ("work", C.c_double * len(PROF_CLASSES)),
+                ("launches", C.c_int64 * len(PROF_CLASSES))]
 
     def as_dict(self):
         return {name: dict(ms=self.ms[i], work=self.work[i], launches=self.launches[i])
@@ -128,11 +130,15 @@ def probe_fp64_peak(device=0):
     return v.value
 
 
+PRODUCTS = {"auto": 0, "dense": 1, "sparse": 2}
+
+
 class Handle:
-    """A library handle.  precision: 'fp64', 'tf32x3' or 'bf16x3'."""
+    """A library handle.  precision: 'fp64', 'tf32x3' or 'bf16x3'; products: how the sandwich
+    products are formed, 'auto', 'dense' or 'sparse' (glasso_products)."""
 
     def __init__(self, precision="fp64", device=0, stream=None, max_iter=500, shrink=0.5, t_min=1e-4,
-                 hbm_budget_bytes=0, serve_slots=8):
+                 hbm_budget_bytes=0, serve_slots=8, products="auto"):
         cfg = glasso_config()
         glasso_config_default(C.byref(cfg))
         cfg.device = device
@@ -143,6 +149,7 @@ class Handle:
         cfg.t_min = t_min
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.serve_slots = serve_slots
+        cfg.products = PRODUCTS[products]
         h = C.c_void_p()
         st = glasso_create(C.byref(cfg), C.byref(h))
         if st != OK:

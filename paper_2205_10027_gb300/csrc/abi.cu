@@ -69,6 +69,7 @@ glasso_status glasso_config_default(glasso_config* cfg) {
   cfg->t_min = 1e-4;
   cfg->hbm_budget_bytes = 0;
   cfg->serve_slots = 8;
+  cfg->products = GLASSO_PRODUCTS_AUTO;
   return GLASSO_OK;
 }
 
@@ -79,6 +80,7 @@ glasso_status glasso_create(const glasso_config* cfg_in, glasso_handle** out) {
   if (cfg_in) cfg = *cfg_in; else glasso_config_default(&cfg);
   if (cfg.precision < GLASSO_FP64 || cfg.precision > GLASSO_MIXED_BF16X3) return GLASSO_ERR_ARG;
   if (cfg.serve_slots <= 0) cfg.serve_slots = 8;
+  if (cfg.products < GLASSO_PRODUCTS_AUTO || cfg.products > GLASSO_PRODUCTS_SPARSE) return GLASSO_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();

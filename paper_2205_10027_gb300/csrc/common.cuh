@@ -55,6 +55,11 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
   return s;
 }
 
+// *addr = max(*addr, v) for non-negative doubles (which order like their bit patterns).
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
 __device__ __forceinline__ double sgn(double x) { return (x > 0.0) - (x < 0.0); }
 
 // SoftThreshold(v, c) = sign(v) max(|v| - c, 0)  (App. A.1).

@@ -27,10 +27,6 @@ __device__ __forceinline__ bool abs_greater(double g, uint64_t lam_bits) {
   return ((uint64_t)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull) > lam_bits;
 }
 
-__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
-}
 
 // ---- S: copy the lower triangle of the caller's n x n S into the padded FP64 buffer,
 //      mirrored, and record max |S_ij - S_ji|, max |S_ij|, non-finite count, min S_ii.
@@ -455,6 +451,11 @@ void logdet_difference_terms(const double* At, const double* A, const double* W,
                              cudaStream_t st) {
   k_rows_times_W<<<(int)n, QT, 0, st>>>(At, A, W, ld, n, np, 1.0, 0, Q, nullptr);
   LAUNCH_CHECK();
+  trace_terms(Q, ld, n, np, parts, out2, st);
+}
+
+void trace_terms(const double* Q, int64_t ld, int64_t n, int np, double* parts, double* out2,
+                 cudaStream_t st) {
   const int nt = np / 32;
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int g = (int)std::min<int64_t>(ntiles, kRedBlocks);

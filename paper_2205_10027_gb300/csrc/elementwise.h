@@ -31,6 +31,9 @@ void objective_terms(const double* S, const double* A, int64_t ld, int64_t n, do
 void logdet_difference_terms(const double* At, const double* A, const double* W, int64_t ld,
                              int64_t n, int np, double* Q, double* parts, double* out2,
                              cudaStream_t st);
+// out2 = {tr(Q), tr(Q^2)} of a given Q (its n x n block).
+void trace_terms(const double* Q, int64_t ld, int64_t n, int np, double* parts, double* out2,
+                 cudaStream_t st);
 // R = I - A W in FP64 over the padded size (padding of R zero), with the nonzeros of each
 // row of A compacted first; *rmax = max |R_ij| over the n x n block.
 void inverse_residual(const double* A, const double* W, int64_t ld, int64_t n, int np, double* R,

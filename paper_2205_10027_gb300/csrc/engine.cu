@@ -47,6 +47,9 @@ __global__ void k_fill(double* x, int64_t n, double v) {
   if (j < n) x[j] = v;
 }
 
+// CSR capacity of the sparse sandwich: 256 nonzeros per row on average
+int64_t csr_cap(int np) { return (int64_t)256 * np; }
+
 template <typename T>
 void dfree(T*& p) {
   if (p) cudaFree((void*)p);
@@ -59,13 +62,16 @@ void dfree(T*& p) {
 // ------------------------------------------------------------------------------------------
 size_t Workspace::bytes_for(int np) {
   const size_t m = (size_t)np * np;
-  return 11 * m * sizeof(double) + m + tc_scratch_bytes_for(np);
+  const size_t csr = (size_t)(np + 1) * 8 + (size_t)np * 4 + (size_t)csr_cap(np) * 12;
+  return 11 * m * sizeof(double) + m + tc_scratch_bytes_for(np) + csr;
 }
 
 void Workspace::release() {
   dfree(S); dfree(A); dfree(At); dfree(W); dfree(L); dfree(Lt); dfree(X); dfree(Y); dfree(T);
   dfree(code); dfree(Li); dfree(Lti); dfree(ld_parts); dfree(parts); dfree(sc);
   dfree(pd); dfree(vmax); dfree(bad); dfree(vec);
+  dfree(csr.rowptr); dfree(csr.col); dfree(csr.val); dfree(counts);
+  csr.cap = 0;
   if (staging) cudaFree(staging);
   staging = nullptr;
   staging_bytes = 0;
@@ -106,6 +112,11 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
     alloc(vmax, 2 * sizeof(double));
     alloc(bad, sizeof(int));
     alloc(vec, (size_t)3 * np_new * 8);
+    alloc(csr.rowptr, (size_t)(np_new + 1) * 8);
+    alloc(counts, (size_t)np_new * 4);
+    csr.cap = csr_cap(np_new);
+    alloc(csr.col, (size_t)csr.cap * 4);
+    alloc(csr.val, (size_t)csr.cap * 8);
     tc_scratch_bytes = tc_scratch_bytes_for(np_new);
     if (tc_scratch_bytes) alloc(tc_scratch, tc_scratch_bytes);
     if (cudaMallocHost((void**)&hs, sizeof(Scalars)) != cudaSuccess) {
@@ -380,6 +391,12 @@ void Engine::factor_graphed(double* L, double* Li, cudaStream_t st) {
 void Engine::compute_inverse(double* Li, cudaStream_t st) {
   if (panel_ > 0) inverse_merge(ws.L, Li, ws.ld, ws.np, ws.T, panel_, gemm_fn(), st);
   inverse_from_inverse_factor(Li, ws.ld, ws.np, ws.W, gemm_fn(), st);
+  {
+    Profiler::Rec rec;
+    prof.begin_rec(GLASSO_PROF_AUX, 8.0 * (double)ws.np * (double)ws.np, st, rec);
+    mirror_lower(ws.W, ws.ld, ws.np, st);
+    prof.end_rec(rec, st);
+  }
   if (cfg_.precision != GLASSO_FP64) refine_inverse(st);
 }
 
@@ -392,8 +409,21 @@ void Engine::refine_inverse(cudaStream_t st) {
   const int np = ws.np;
   const int64_t ld = ws.ld;
   double* rmax = &ws.sc->aux[0];
+  const double nn = (double)np * (double)np;
   for (int sweep = 0; sweep < 3; ++sweep) {
-    inverse_residual(ws.A, ws.W, ld, ws.n, np, ws.T, rmax, st);
+    {
+      // the residual is a sparse-dense product: through the CSR of A when it fits
+      const bool csr = ensure_csr_of_A(st);
+      Profiler::Rec rec;
+      prof.begin_rec(GLASSO_PROF_RESIDUAL, 16.0 * nn, st, rec);
+      if (csr) {
+        CUDA_CHECK(cudaMemsetAsync(rmax, 0, sizeof(double), st));
+        spmm_residual(ws.csr, ws.W, ld, ws.T, ld, ws.n, np, rmax, st);
+      } else {
+        inverse_residual(ws.A, ws.W, ld, ws.n, np, ws.T, rmax, st);
+      }
+      prof.end_rec(rec, st);
+    }
     double h = 0.0;
     CUDA_CHECK(cudaMemcpyAsync(&h, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
@@ -402,14 +432,66 @@ void Engine::refine_inverse(cudaStream_t st) {
     GemmArgs g = gemm_args(ws.W, ld, 0, ws.T, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
     g.lower = 1;
     gemm(g, GemmRole::Refine, st);
-    add_lower_mirror(ws.W, ws.Y, ld, np, st);
+    {
+      Profiler::Rec rec;
+      prof.begin_rec(GLASSO_PROF_AUX, 16.0 * nn, st, rec);
+      add_lower_mirror(ws.W, ws.Y, ld, np, st);
+      prof.end_rec(rec, st);
+    }
     if (h * h + 1e-6 * h < 1e-11) break;  // the sweep just made has brought it below 1e-10
   }
 }
 
-// Y = lower(A X A): T = A X, then Y = T A on the lower triangle (Y is symmetric)
-void Engine::sandwich(cudaStream_t st) {
+bool Engine::ensure_csr_of_A(cudaStream_t st) {
+  if (csr_valid_) return true;
+  csr_rowptr(ws.A, nullptr, ws.ld, ws.n, ws.np, ws.counts, ws.csr.rowptr, st);
+  int64_t nnz = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&nnz, ws.csr.rowptr + ws.np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  if (nnz > ws.csr.cap) return false;
+  csr_fill(ws.A, nullptr, ws.ld, ws.n, ws.np, ws.csr, st);
+  csr_valid_ = true;
+  return true;
+}
+
+// log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3), E similar to
+// Q = (At - A) W; (At - A) is nonzero only where the step changed an entry, so Q is a sparse-
+// dense product (through a CSR of the difference when at most nnz_bound entries fit).
+void Engine::logdet_terms(double nnz_bound, cudaStream_t st) {
+  const int64_t n = st_.n;
+  Profiler::Rec rec;
+  prof.begin_rec(GLASSO_PROF_LOGDET2, 32.0 * (double)n * (double)n, st, rec);
+  if (nnz_bound <= (double)ws.csr.cap) {
+    csr_valid_ = false;  // the CSR buffers now hold the difference
+    csr_rowptr(ws.At, ws.A, ws.ld, n, ws.np, ws.counts, ws.csr.rowptr, st);
+    csr_fill(ws.At, ws.A, ws.ld, n, ws.np, ws.csr, st);
+    spmm(ws.csr, ws.W, ws.ld, ws.T, ws.ld, ws.np, false, false, st);
+    trace_terms(ws.T, ws.ld, n, ws.np, ws.parts, &ws.sc->tr_e, st);
+  } else {
+    logdet_difference_terms(ws.At, ws.A, ws.W, ws.ld, n, ws.np, ws.T, ws.parts, &ws.sc->tr_e, st);
+  }
+  prof.end_rec(rec, st);
+}
+
+bool Engine::sparse_sandwich(double nnz) const {
+  if (cfg_.products == GLASSO_PRODUCTS_DENSE || nnz > (double)ws.csr.cap) return false;
+  if (cfg_.products == GLASSO_PRODUCTS_SPARSE || cfg_.precision == GLASSO_FP64) return true;
+  const double n = (double)ws.n;
+  return nnz <= n * std::max(16.0, n / 256.0);
+}
+
+// Y = lower(A X A).  Sparse: T = (A X)^T = X A from the CSR of A, then Y = A T.  Dense:
+// T = A X, then Y = T A on the lower triangle (Y is symmetric).
+void Engine::sandwich(double nnz, cudaStream_t st) {
   const int np = ws.np;
+  if (sparse_sandwich(nnz) && ensure_csr_of_A(st)) {
+    Profiler::Rec rec;
+    prof.begin_rec(GLASSO_PROF_SPMM, 3.0 * nnz * (double)np, st, rec);
+    spmm(ws.csr, ws.X, ws.ld, ws.T, ws.ld, np, true, false, st);
+    spmm(ws.csr, ws.T, ws.ld, ws.Y, ws.ld, np, false, true, st);
+    prof.end_rec(rec, st);
+    return;
+  }
   GemmArgs a = gemm_args(ws.A, ws.ld, 0, ws.X, ws.ld, 0, ws.T, ws.ld, np, np, np, 1.0, 0.0);
   gemm(a, GemmRole::Sandwich, st);
   GemmArgs b = gemm_args(ws.T, ws.ld, 0, ws.A, ws.ld, 0, ws.Y, ws.ld, np, np, np, 1.0, 0.0);
@@ -443,6 +525,7 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   st_.launches_begin = tl_launches;
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   const int np = ws.np;
   const int64_t ld = ws.ld;
@@ -487,6 +570,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   const double shrink = cfg_.shrink > 0 && cfg_.shrink < 1 ? cfg_.shrink : 0.5;
   const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
 
+  csr_valid_ = false;  // A changed since the last step (or the CSR holds a difference)
   compute_inverse(ws.Li, st);
   {
     Profiler::Rec rec;
@@ -500,7 +584,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   out.nnz = h.nnz;
   if (out.r <= tol) return GLASSO_OK;
   if (st_.k >= max_iter) return GLASSO_MAX_ITER;
-  sandwich(st);
+  sandwich(h.nnz, st);
   // rounding allowance of F: FP64 unit roundoff, or the split products' for the mixed modes
   // (whose Cholesky trailing updates carry about 2^-21 relative error)
   const double u = cfg_.precision == GLASSO_FP64 ? kUnitRoundoff : std::ldexp(1.0, -21);
@@ -525,7 +609,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
     double d = -(h.logdet_t - st_.ld_A) + lin;
     if (std::fabs(d) <= kDiffBand * delta) {
       // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3)
-      logdet_difference_terms(ws.At, ws.A, ws.W, ld, n, np, ws.T, ws.parts, &ws.sc->tr_e, st);
+      logdet_terms(h.nnz + h.nnz_t, st);
       sync_scalars();
       // the series is used while |E|_F <= 0.1, where its truncation (<= |E|_F^3 / 2.7) stays
       // far below the second-order term; otherwise the Cholesky difference stands
@@ -604,6 +688,7 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
 void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.Lt, false);
   pad_identity(ws.Lt, ws.ld, n, ws.np, st);
@@ -618,6 +703,7 @@ void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double*
 int Engine::op_inverse(const double* A, int64_t n, double* W) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   pad_identity(ws.A, ws.ld, n, ws.np, st);
@@ -635,6 +721,7 @@ void Engine::op_gradient(const double* S, const double* A, const double* W, int6
                          double* X, int8_t* code, double sums[4]) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(S, false, true, n, ws.S, false);
   load_matrix(A, false, true, n, ws.A, false);
@@ -649,10 +736,16 @@ void Engine::op_gradient(const double* S, const double* A, const double* W, int6
 void Engine::op_sandwich(const double* A, const double* X, int64_t n, double* Y) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   load_matrix(X, false, true, n, ws.X, false);
-  sandwich(st);
+  // nnz of A from its CSR row pointers
+  csr_rowptr(ws.A, nullptr, ws.ld, n, ws.np, ws.counts, ws.csr.rowptr, st);
+  int64_t nnz = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&nnz, ws.csr.rowptr + ws.np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  sandwich((double)nnz, st);
   mirror_lower(ws.Y, ws.ld, ws.np, st);
   unpad(ws.Y, ws.ld, n, Y, st);
   CUDA_CHECK(cudaStreamSynchronize(st));
@@ -662,6 +755,7 @@ void Engine::op_trial(const double* A, const double* Y, const int8_t* code, int6
                       double t, double* At) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  csr_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   load_matrix(Y, false, true, n, ws.Y, false);

@@ -10,6 +10,7 @@
 #include "../../include/glasso.h"
 #include "elementwise.h"
 #include "factor.h"
+#include "sparse.h"
 
 namespace glasso {
 
@@ -34,6 +35,8 @@ struct Workspace {
   size_t staging_bytes = 0;
   void* tc_scratch = nullptr;             // split operands of the tensor-core GEMMs
   size_t tc_scratch_bytes = 0;
+  Csr csr;                                // Theta in CSR form for the sparse sandwich
+  int* counts = nullptr;                  // np per-row nonzero counts
   uint64_t epoch = 0;                     // bumped at every reallocation
 
   static size_t bytes_for(int np);
@@ -121,7 +124,15 @@ class Engine {
 
  private:
   void load_matrix(const void* src, bool f32, bool on_device, int64_t n, double* dst, bool check_s);
-  void sandwich(cudaStream_t st);
+  // Y = lower(A X A): sparse products while nnz(A) (over the n x n block) permits, else dense
+  void sandwich(double nnz, cudaStream_t st);
+  bool sparse_sandwich(double nnz) const;
+  // CSR of ws.A in ws.csr (built at most once per outer iteration); false when nnz(A)
+  // exceeds the capacity
+  bool ensure_csr_of_A(cudaStream_t st);
+  bool csr_valid_ = false;
+  // Q = (At - A) W and {tr Q, tr Q^2} into the scalars
+  void logdet_terms(double nnz_bound, cudaStream_t st);
   void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);

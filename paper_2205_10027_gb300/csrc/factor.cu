@@ -16,86 +16,194 @@ constexpr int NB = kNb;        // leaf size of the FP64 form (64)
 constexpr int NB32 = 128;      // leaf size of the split-precision forms (FP32 leaves)
 
 // Factor the NB x NB diagonal block at Ablk (leading dimension ld) in place, write the
-// inverse of its factor to Xblk (leading dimension ld, zero upper), 2 sum log L_jj to
-// *ld_part, and clear *pd on a pivot that is not finite and positive.  T is the arithmetic
-// type: double for the FP64 form, float for the split-precision forms (whose products carry
-// FP32-level error anyway); storage and the log det are FP64 in both.
+// inverse of its factor to the lower triangle of Xblk (leading dimension ld; the caller has
+// zeroed X), 2 sum log L_jj to *ld_part, and clear *pd on a pivot that is not finite and
+// positive.  T is the arithmetic type: double for the FP64 form, float for the
+// split-precision forms (whose products carry FP32-level error anyway); storage and the log
+// det are FP64 in both.
 //
-// Blocked by 32 columns so that barriers are few: warp 0 factors each 32 x 32 diagonal block
-// with one row per lane in registers (pivots and columns travel by shuffles), then the rows
-// below solve against it one row per thread, and all warps apply the rank-32 update.  The
-// inverse inverts the diagonal 32 x 32 blocks one warp each (one column per lane), then fills
-// the block rows below: X_ij = -X_ii (sum_{j<=k<i} L_ik X_kj).
+// One CTA, blocked by 32-column panels p, two barriers per panel:
+//  (1) warp 0 factors the 32 x 32 diagonal block L_pp, one row per lane in registers, and in
+//      the same sweep applies the inverse elementary column transforms to an identity held
+//      the same way, which leaves X_pp = L_pp^{-1};
+//  (2) all warps: the rows below, L_ip = A_ip X_pp^T (dot products of length 32), and the
+//      first half of block row p of X, T_pj = sum_{j<=k<p} L_pk X_kj (into the unused upper
+//      triangle of the block);
+//  (3) all warps: the rank-32 update of the trailing lower triangle, and X_pj = -X_pp T_pj.
+// Work items are 8 rows x 32 columns (one column per lane), so each shared-memory load of a
+// row segment is a 16-byte broadcast reused by the 8 accumulators of a lane.
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T& v0, T& v1, T& v2, T& v3);
+template <>
+__device__ __forceinline__ void lds4<float>(const float* p, float& v0, float& v1, float& v2, float& v3) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v0 = q.x; v1 = q.y; v2 = q.z; v3 = q.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(const double* p, double& v0, double& v1, double& v2, double& v3) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+  v0 = q0.x; v1 = q0.y; v2 = q1.x; v3 = q1.y;
+}
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+
+// acc[q] += sum_{k in [k0, k1)} R[(r0 + q) * LDS + k] * c[k]  for q < 8, with c[k] supplied
+// by the caller as a per-lane register row (k relative to 0) or a strided shared column.
+template <typename T, int LDS>
+__device__ __forceinline__ void rows8_times_regs(const T* R, int r0, int koff, const T (&c)[32], T (&acc)[8]) {
+#pragma unroll
+  for (int k = 0; k < 32; k += 4) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      T v0, v1, v2, v3;
+      lds4(R + (r0 + q) * LDS + koff + k, v0, v1, v2, v3);
+      acc[q] = fma(v0, c[k], acc[q]);
+      acc[q] = fma(v1, c[k + 1], acc[q]);
+      acc[q] = fma(v2, c[k + 2], acc[q]);
+      acc[q] = fma(v3, c[k + 3], acc[q]);
+    }
+  }
+}
+
+// Step J of the 32 x 32 diagonal-block sweep in one warp (lane l holds row l of the block
+// in r and row l of the running inverse in xr): pivot d = L_JJ^2, column J of L, the inverse
+// elementary transform E_J^{-1} on xr, and the right-looking update of columns > J.  Written
+// as a template recursion so that every register index is a compile-time constant.
+// Entries of r above the diagonal (r[c], c > lane) are scratch: they take updates that are
+// never read back, which keeps every update a plain multiply-add (no per-lane predicate).
+template <typename T, int J>
+__device__ __forceinline__ void diag_steps(T (&r)[32], T (&xr)[32], int lane, bool& bad) {
+  if constexpr (J < 32) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const T d = __shfl_sync(FULL, r[J], J);  // pivot after the updates of columns < J
+    bad |= !(d > T(0)) || isinf(d);
+    const T s = rsqrt_t(d);  // 1 / L_JJ
+    r[J] = (lane == J) ? d * s : r[J] * s;  // column J of L (valid for lanes >= J)
+    // xr <- E_J^{-1} xr: row J scaled by 1 / L_JJ, rows below minus L_iJ (row J)
+    const T sj = (lane == J) ? s : T(1);
+#pragma unroll
+    for (int c = 0; c <= J; ++c) xr[c] *= sj;
+    const T m = (lane > J) ? -r[J] : T(0);
+#pragma unroll
+    for (int c = 0; c <= J; ++c) xr[c] = fma(m, __shfl_sync(FULL, xr[c], J), xr[c]);
+    // right-looking update of columns > J (rows >= c are the valid ones)
+    const T mr = -r[J];
+#pragma unroll
+    for (int c = J + 1; c < 32; ++c) r[c] = fma(mr, __shfl_sync(FULL, r[J], c), r[c]);
+    diag_steps<T, J + 1>(r, xr, lane, bad);
+  }
+}
+
 template <typename T, int NB, int PT>
-__global__ void __launch_bounds__(PT) k_potrf_diag(double* Ablk, int64_t ld, double* Xblk,
-                                                   double* ld_part, int* pd) {
-  constexpr int LDS = NB + 1;  // padded shared row
-  constexpr int P = NB / 32;   // 32-column panels
+__global__ void __launch_bounds__(PT) k_leaf_chol_inv(double* Ablk, int64_t ld, double* Xblk,
+                                                      double* ld_part, int* pd) {
+  constexpr int LDS = NB + 4;  // row pitch: rows start on 16-byte boundaries
+  constexpr int P = NB / 32;
   constexpr int NW = PT / 32;
-  static_assert(NB % 32 == 0 && NW >= P, "one warp per diagonal block in the inverse");
+  constexpr unsigned FULL = 0xffffffffu;
+  static_assert(NB % 32 == 0 && PT % 32 == 0, "shape");
   if (*pd == 0) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* a = reinterpret_cast<T*>(sm_raw);  // [NB][LDS]
-  T* x = a + NB * LDS;                  // [NB][LDS]
+  T* a = reinterpret_cast<T*>(sm_raw);  // [NB][LDS]: L (lower); T_pj scratch above the diagonal
+  T* x = a + NB * LDS;                  // [NB][LDS]: X = L^{-1} (lower, zero above)
   __shared__ double red[32];
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < NB * NB; e += PT) {
     const int i = e / NB, c = e % NB;
-    a[i * LDS + c] = (c <= i) ? from_f64<T>(Ablk[(int64_t)i * ld + c]) : (T)0;
-    x[i * LDS + c] = (T)0;
+    a[i * LDS + c] = (c <= i) ? from_f64<T>(Ablk[(int64_t)i * ld + c]) : T(0);
+    x[i * LDS + c] = T(0);
   }
   if (tid == 0) fail = 0;
   __syncthreads();
 
   for (int p = 0; p < P; ++p) {
     const int o = 32 * p;
-    // (1) 32 x 32 diagonal block, lane r holding row o + r
+    const int m = NB - o - 32;  // trailing rows
+    // ---- (1) L_pp and X_pp in warp 0
     if (warp == 0) {
-      T row[32];
+      T r[32], xr[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) row[c] = (c <= lane) ? a[(o + lane) * LDS + o + c] : (T)0;
+      for (int c = 0; c < 32; ++c) {
+        r[c] = (c <= lane) ? a[(o + lane) * LDS + o + c] : T(0);
+        xr[c] = (c == lane) ? T(1) : T(0);
+      }
       bool bad = false;
+      diag_steps<T, 0>(r, xr, lane, bad);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const T d = __shfl_sync(0xffffffffu, row[j], j);
-        if (!(d > (T)0) || !isfinite(d)) bad = true;
-        const T piv = sqrt(d);
-        if (lane == j) row[j] = piv;
-        if (lane > j) row[j] = row[j] / piv;
-#pragma unroll
-        for (int c = j + 1; c < 32; ++c) {
-          const T lcj = __shfl_sync(0xffffffffu, row[j], c);
-          if (lane >= c) row[c] -= row[j] * lcj;
+      for (int c = 0; c < 32; ++c) {
+        if (c <= lane) {
+          a[(o + lane) * LDS + o + c] = r[c];
+          x[(o + lane) * LDS + o + c] = xr[c];
         }
       }
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c <= lane) a[(o + lane) * LDS + o + c] = row[c];
-      if (lane == 0 && bad) fail = 1;
+      if (__any_sync(FULL, bad) && lane == 0) fail = 1;
     }
     __syncthreads();
     if (fail) break;
-    // (2) rows below: l_i = a_i L_pp^{-T}, one row per thread (forward substitution)
-    for (int i = o + 32 + tid; i < NB; i += PT) {
-      T* ri = a + i * LDS + o;
-      for (int j = 0; j < 32; ++j) {
-        const T* lj = a + (o + j) * LDS + o;
-        T s = ri[j];
-        for (int k = 0; k < j; ++k) s -= ri[k] * lj[k];
-        ri[j] = s / lj[j];
+    // ---- (2) rows below: L_ip = A_ip X_pp^T;  T_pj = sum_{j<=k<p} L_pk X_kj
+    {
+      const int n_rows = m / 8, n_t = 4 * p;
+      for (int t = warp; t < n_rows + n_t; t += NW) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = T(0);
+        if (t < n_rows) {
+          T xrow[32];  // row `lane` of X_pp
+#pragma unroll
+          for (int k = 0; k < 32; k += 4)
+            lds4(x + (o + lane) * LDS + o + k, xrow[k], xrow[k + 1], xrow[k + 2], xrow[k + 3]);
+          const int r0 = o + 32 + 8 * t;
+          rows8_times_regs<T, LDS>(a, r0, o, xrow, acc);
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[(r0 + q) * LDS + o + lane] = acc[q];
+        } else {
+          const int u = t - n_rows, j = u / 4, r0 = 8 * (u % 4);
+          // rows o + r0 .. + 7 of L against column 32 j + lane of X, k over [32 j, o)
+          for (int k0 = 32 * j; k0 < o; k0 += 32) {
+            T col[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) col[k] = x[(k0 + k) * LDS + 32 * j + lane];
+            rows8_times_regs<T, LDS>(a, o + r0, k0, col, acc);
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[(32 * j + r0 + q) * LDS + o + lane] = acc[q];
+        }
       }
     }
     __syncthreads();
-    // (3) rank-32 update of the trailing lower triangle; warp w takes rows o+32+w, +NW, ...
-    for (int i = o + 32 + warp; i < NB; i += NW) {
-      const T* ri = a + i * LDS + o;
-      for (int c = o + 32 + lane; c <= i; c += 32) {
-        const T* rc = a + c * LDS + o;
-        T s = (T)0;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) s += ri[k] * rc[k];
-        a[i * LDS + c] -= s;
+    // ---- (3) trailing update A_ic -= sum_k L_ik L_ck (o+32 <= c <= i);  X_pj = -X_pp T_pj
+    {
+      int n_upd = 0;
+      for (int q = 0; q < m / 32; ++q) n_upd += (m - 32 * q) / 8;
+      const int n_x = 4 * p;
+      for (int t = warp; t < n_upd + n_x; t += NW) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = T(0);
+        if (t < n_upd) {
+          int chunk = 0, rem = t;
+          while (rem >= (m - 32 * chunk) / 8) { rem -= (m - 32 * chunk) / 8; ++chunk; }
+          const int c = o + 32 + 32 * chunk + lane;
+          const int r0 = o + 32 + 32 * chunk + 8 * rem;
+          T lc[32];  // row c of the panel: L_c,o..o+31
+#pragma unroll
+          for (int k = 0; k < 32; k += 4) lds4(a + c * LDS + o + k, lc[k], lc[k + 1], lc[k + 2], lc[k + 3]);
+          rows8_times_regs<T, LDS>(a, r0, o, lc, acc);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (c <= r0 + q) a[(r0 + q) * LDS + c] -= acc[q];
+        } else {
+          const int u = t - n_upd, j = u / 4, r0 = 8 * (u % 4);
+          T col[32];  // column 32 j + lane of T_pj (stored at rows 32 j.., columns o..)
+#pragma unroll
+          for (int k = 0; k < 32; ++k) col[k] = a[(32 * j + k) * LDS + o + lane];
+          rows8_times_regs<T, LDS>(x, o + r0, o, col, acc);  // X_pp is zero above its diagonal
+#pragma unroll
+          for (int q = 0; q < 8; ++q) x[(o + r0 + q) * LDS + 32 * j + lane] = -acc[q];
+        }
       }
     }
     __syncthreads();
@@ -104,56 +212,18 @@ __global__ void __launch_bounds__(PT) k_potrf_diag(double* Ablk, int64_t ld, dou
     if (tid == 0) *pd = 0;
     return;
   }
-  // inverse: diagonal blocks, one warp each, one column per lane
-  if (warp < P) {
-    const int o = 32 * warp, c = lane;
-    for (int r = 0; r < 32; ++r) {
-      if (r < c) continue;
-      T s = (r == c) ? (T)1 : (T)0;
-      for (int k = c; k < r; ++k) s -= a[(o + r) * LDS + o + k] * x[(o + k) * LDS + o + c];
-      x[(o + r) * LDS + o + c] = s / a[(o + r) * LDS + o + r];
-    }
-  }
-  __syncthreads();
-  // block rows below: X_ij = -X_ii (sum_{j<=k<i} L_ik X_kj) for j < i, through the upper
-  // (unused) half of a as scratch is not safe; use x's own block (i, j) for the sum first
-  for (int bi = 1; bi < P; ++bi) {
-    // S_ij = sum_k L_ik X_kj into x block (bi, j) for all j < bi
-    for (int e = tid; e < bi * 32 * 32; e += PT) {
-      const int j = e / 1024, r = (e / 32) % 32, c = e % 32;
-      const int gi = 32 * bi + r, gj = 32 * j + c;
-      T s = (T)0;
-      for (int k = 32 * j; k < 32 * bi; ++k) s += a[gi * LDS + k] * x[k * LDS + gj];
-      x[gi * LDS + gj] = s;
-    }
-    __syncthreads();
-    // X_ij = -X_ii S_ij, computed into registers first (S is overwritten in place)
-    T v[(NB * 32 + PT - 1) / PT];
-    int cnt = 0;
-    for (int e = tid; e < bi * 32 * 32; e += PT, ++cnt) {
-      const int j = e / 1024, r = (e / 32) % 32, c = e % 32;
-      const int gi = 32 * bi + r, gj = 32 * j + c;
-      T s = (T)0;
-      for (int k = 0; k <= r; ++k) s += x[gi * LDS + 32 * bi + k] * x[(32 * bi + k) * LDS + gj];
-      v[cnt] = -s;
-    }
-    __syncthreads();
-    cnt = 0;
-    for (int e = tid; e < bi * 32 * 32; e += PT, ++cnt) {
-      const int j = e / 1024, r = (e / 32) % 32, c = e % 32;
-      x[(32 * bi + r) * LDS + 32 * j + c] = v[cnt];
-    }
-    __syncthreads();
-  }
-  const double lsum = (tid < NB) ? log((double)a[tid * LDS + tid]) : 0.0;
+  const double lsum = (tid < NB) ? log(to_f64(a[tid * LDS + tid])) : 0.0;
   const double tot = block_sum(lsum, red);
   for (int e = tid; e < NB * NB; e += PT) {
     const int i = e / NB, c = e % NB;
     Ablk[(int64_t)i * ld + c] = (c <= i) ? to_f64(a[i * LDS + c]) : 0.0;
-    Xblk[(int64_t)i * ld + c] = to_f64(x[i * LDS + c]);
+    if (c <= i) Xblk[(int64_t)i * ld + c] = to_f64(x[i * LDS + c]);
   }
   if (tid == 0) *ld_part = 2.0 * tot;
 }
+
+// dynamic shared memory of k_leaf_chol_inv: two NB x (NB + 4) arrays
+constexpr size_t leaf_smem(int nb, size_t elt) { return 2 * (size_t)nb * (nb + 4) * elt; }
 
 // out = sum of parts[0..n) in index order (one thread: n is at most a few hundred).
 __global__ void k_sum_parts(const double* parts, int n, const int* pd, double* out) {
@@ -209,9 +279,9 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
     double* Ab = c.A + (int64_t)o * c.ld + o;
     double* Xb = c.X + (int64_t)o * c.ld + o;
     if (c.fp32_leaf)
-      k_potrf_diag<float, NB32, 4 * NB32><<<1, 4 * NB32, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
+      k_leaf_chol_inv<float, NB32, 4 * NB32><<<1, 4 * NB32, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
     else
-      k_potrf_diag<double, NB, 4 * NB><<<1, 4 * NB, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
+      k_leaf_chol_inv<double, NB, 4 * NB><<<1, 4 * NB, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
     LAUNCH_CHECK();
     return;
   }
@@ -255,15 +325,15 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
                       double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf, int panel) {
   const int leaf = fp32_leaf ? NB32 : NB;
-  const size_t smem = 2 * (size_t)leaf * (leaf + 1) * (fp32_leaf ? sizeof(float) : sizeof(double));
+  const size_t smem = leaf_smem(leaf, fp32_leaf ? sizeof(float) : sizeof(double));
   static std::once_flag once;  // not repeated inside a stream capture
   std::call_once(once, [] {
-    CUDA_CHECK(cudaFuncSetAttribute(k_potrf_diag<float, NB32, 4 * NB32>,
+    CUDA_CHECK(cudaFuncSetAttribute(k_leaf_chol_inv<float, NB32, 4 * NB32>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(2 * NB32 * (NB32 + 1) * sizeof(float))));
-    CUDA_CHECK(cudaFuncSetAttribute(k_potrf_diag<double, NB, 4 * NB>,
+                                    (int)leaf_smem(NB32, sizeof(float))));
+    CUDA_CHECK(cudaFuncSetAttribute(k_leaf_chol_inv<double, NB, 4 * NB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(2 * NB * (NB + 1) * sizeof(double))));
+                                    (int)leaf_smem(NB, sizeof(double))));
   });
   CUDA_CHECK(cudaMemsetAsync(X, 0, sizeof(double) * ld * np, st));
   Ctx c{fp32_leaf, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem};
@@ -328,12 +398,11 @@ void mirror_lower(double* M, int64_t ld, int np, cudaStream_t st) {
 
 void inverse_from_inverse_factor(const double* X, int64_t ld, int np, double* W, const GemmFn& gemm,
                                  cudaStream_t st) {
-  // W = X^T X (lower triangle), then mirrored
+  // W = X^T X (lower triangle; the caller mirrors it)
   GemmArgs w = gemm_args(X, ld, 1, X, ld, 0, W, ld, np, np, np, 1.0, 0.0);
   w.lower = 1;
   w.krule = KR_LO_ROW;
   gemm(w, GemmRole::Inverse, st);
-  mirror_lower(W, ld, np, st);
 }
 
 }  // namespace glasso

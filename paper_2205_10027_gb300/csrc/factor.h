@@ -28,7 +28,8 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
 void inverse_merge(const double* L, double* X, int64_t ld, int np, double* T, int panel, const GemmFn& gemm,
                    cudaStream_t st);
 
-// W = X^T X = (L L^T)^{-1} from X = L^{-1} (lower), written in full.
+// W = X^T X = (L L^T)^{-1} from X = L^{-1} (lower): the lower triangle of W (mirror_lower
+// completes it).
 void inverse_from_inverse_factor(const double* X, int64_t ld, int np, double* W, const GemmFn& gemm,
                                  cudaStream_t st);
 

@@ -2,29 +2,46 @@
 //
 // Each FP64 operand is split into hi + lo parts of a narrow type (TF32 or BF16); the product
 // op(A) op(B) is formed as hi*hi + hi*lo + lo*hi by tcgen05.mma with FP32 accumulation in
-// TMEM, and the epilogue writes alpha * acc + beta * C (FP32 arithmetic, FP64 storage).  One CTA computes a
-// 128 x 128 output tile: one thread issues TMA loads of the four 128 x (128 bytes) operand
-// tiles of a k-stage into a 3-stage shared-memory ring (128-byte swizzle), one thread issues
-// the MMAs, and all four warps drain the accumulator with tcgen05.ld.  Every wait on an
-// mbarrier is bounded; on a timeout the CTA records an error and leaves without writing.
+// TMEM, and the epilogue writes alpha * acc + beta * C (FP32 arithmetic, FP64 storage).  One
+// CTA computes a 128 x TN output tile: one thread issues TMA loads of the four operand tiles
+// of a k-stage (A_hi, A_lo: 128 rows; B_hi, B_lo: TN rows; KB bytes of K per row) into a
+// shared-memory ring, one thread issues the MMAs, and all warps drain the accumulator with
+// tcgen05.ld.  Two shapes: 128 x 256 tiles with 4 stages of 64-byte-swizzled K-slices (the
+// default: twice the MMA work per staged byte of A, and a deeper ring), and 128 x 128 tiles
+// with 3 stages of 128-byte-swizzled slices.  Every wait on an mbarrier is bounded; on a
+// timeout the CTA records an error and leaves without writing.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cstdlib>
 #include "engine.h"
 #include "gemm_tc.h"
 
 namespace glasso {
 
 namespace {
-constexpr int TM = 128, TN = 128;
-constexpr int STAGES = 3;
-constexpr int THREADS = 128;
-constexpr uint32_t TMEM_COLS = 128;
-constexpr int TILE_BYTES = 128 * 128;          // 128 rows x 128 bytes of K
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TM = 128;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at 2 GHz
 constexpr int GROUP_M = 12;
+
+// Tile shape and shared-memory ring of one kernel configuration.
+template <int TN_, int STAGES_, int KB_>
+struct TcCfg {
+  static constexpr int TN = TN_;
+  static constexpr int STAGES = STAGES_;
+  static constexpr int KB = KB_;                          // bytes of K per operand row and stage
+  static constexpr int THREADS = TN == 256 ? 256 : 128;   // epilogue: one warp per 32 x 128 block
+  static constexpr uint32_t TMEM_COLS = TN;               // FP32 accumulator columns
+  static constexpr int A_BYTES = TM * KB;
+  static constexpr int B_BYTES = TN * KB;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr uint64_t LAYOUT = KB == 128 ? 2 : 4;   // descriptor: 128- or 64-byte swizzle
+  static_assert(KB == 128 || KB == 64, "swizzle width");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+using CfgWide = TcCfg<256, 4, 64>;
+using CfgSquare = TcCfg<128, 3, 128>;
 
 struct TcArgs {
   double* C;
@@ -32,7 +49,7 @@ struct TcArgs {
   int M, N, K;
   double alpha, beta;
   int lower, krule;
-  int kstep;          // K elements per 128-byte stage: 32 (TF32) or 64 (BF16)
+  int kstep;          // K elements per stage: KB / element size
   uint32_t idesc;     // tcgen05 instruction descriptor
   const int* flag;
   int* err;
@@ -75,15 +92,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout:
-// rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand tile in a swizzled layout: rows of KB
+// bytes, 8-row groups 8 * KB bytes apart (layout code 2 = 128-byte, 4 = 64-byte swizzle).
+template <int KB, uint64_t LAYOUT>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride between 8-row groups
+  d |= (uint64_t)((8 * KB) >> 4) << 32;      // stride between 8-row groups
   d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= LAYOUT << 61;                         // swizzle mode
   return d;
 }
 
@@ -124,10 +142,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <class CF>
+__global__ void __launch_bounds__(CF::THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               const __grid_constant__ TcArgs p) {
+  constexpr int TN = CF::TN, STAGES = CF::STAGES, STAGE_BYTES = CF::STAGE_BYTES;
+  constexpr int A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
+  constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
   if (p.flag && *p.flag == 0) return;
   // grouped tile order: consecutive blocks walk down a column of GROUP_M tiles, so the
   // CTAs resident at one time cover a near-square patch and share operand panels in L2
@@ -188,9 +210,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_expect_tx(&full[s], STAGE_BYTES);
       const int kx = k_lo + i * p.kstep;
       tma_load_2d(st, &mAh, &full[s], kx, row0);
-      tma_load_2d(st + TILE_BYTES, &mAl, &full[s], kx, row0);
-      tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full[s], kx, col0);
-      tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full[s], kx, col0);
+      tma_load_2d(st + A_BYTES, &mAl, &full[s], kx, row0);
+      tma_load_2d(st + 2 * A_BYTES, &mBh, &full[s], kx, col0);
+      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, &full[s], kx, col0);
       ++issued;
     }
     // do not leave while loads may still land in shared memory
@@ -199,7 +221,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u);
     }
   } else if (warp == 1 && lane == 0 && nk > 0) {
-    // MMA issuer: 4 instructions of 32 bytes along K per stage, three products each
+    // MMA issuer: KB / 32 instructions of 32 bytes along K per stage, three products each
     for (int i = 0; i < nk; ++i) {
       const int s = i % STAGES;
       const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
@@ -207,11 +229,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ah = sw128_desc(base + kk * 32);
-        const uint64_t al = sw128_desc(base + TILE_BYTES + kk * 32);
-        const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
-        const uint64_t bl = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+      for (int kk = 0; kk < CF::KB / 32; ++kk) {
+        const uint64_t ah = sw_desc<CF::KB, CF::LAYOUT>(base + kk * 32);
+        const uint64_t al = sw_desc<CF::KB, CF::LAYOUT>(base + A_BYTES + kk * 32);
+        const uint64_t bh = sw_desc<CF::KB, CF::LAYOUT>(base + 2 * A_BYTES + kk * 32);
+        const uint64_t bl = sw_desc<CF::KB, CF::LAYOUT>(base + 2 * A_BYTES + B_BYTES + kk * 32);
         mma(tmem, al, bh, p.idesc, (i | kk) != 0, tf32);
         mma(tmem, ah, bl, p.idesc, 1, tf32);
         mma(tmem, ah, bh, p.idesc, 1, tf32);
@@ -222,20 +244,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   __syncthreads();
 
-  // epilogue: thread (warp w, lane l) owns row 32 w + l of the tile
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows of the tile) and the
+  // columns of its 128-column half w / 4; thread (w, l) owns row 32 (w % 4) + l
   bool ok = !*s_abort;
   if (ok && nk > 0) ok = mbar_wait(done, 0);
   ok = __syncthreads_and(ok);  // uniform: tcgen05.ld below is warp-collective
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int r = row0 + warp * 32 + lane;
+  const int wq = warp & 3;
+  const int c_first = (warp >> 2) * 4, c_end = min(TN / 32, c_first + 4);
+  const int r = row0 + wq * 32 + lane;
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(p.err, 1);
   } else {
 #pragma unroll 1
-    for (int c = 0; c < TN / 32; ++c) {
+    for (int c = c_first; c < c_end; ++c) {
       float v[32];
       if (nk > 0) {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(c * 32), v);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -382,18 +407,19 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a rows x cols array (row stride ld elements) with 128 x (128 bytes) boxes
-CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld) {
+// 2-D map over a rows x cols array (row stride ld elements) with box_rows x (kb bytes) boxes,
+// swizzled to match the kb-byte rows of the MMA descriptors
+CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld, int box_rows, int kb) {
   CUtensorMap m;
   const int esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), 128};
+  cuuint32_t box[2] = {(cuuint32_t)(kb / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode_fn()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                                  base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                                 kb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(GLASSO_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return m;
 }
@@ -417,7 +443,11 @@ int* g_err = nullptr;  // device error word of the tensor-core kernels
 
 bool tc_available() { return encode_fn() != nullptr; }
 
-size_t tc_scratch_bytes_for(int np) { return (size_t)4 * np * np * sizeof(float) + 256; }
+// A parts padded to 128 rows, B parts to the widest tile (256 rows); 4-byte elements at most
+size_t tc_scratch_bytes_for(int np) {
+  const size_t mp = (size_t)(np + 127) / 128 * 128, npb = (size_t)(np + 255) / 256 * 256;
+  return (2 * mp + 2 * npb) * (size_t)np * sizeof(float) + 256;
+}
 
 bool tc_gemm_supported(const GemmArgs& a) {
   return a.M % 64 == 0 && a.N % 64 == 0 && a.K % 64 == 0 && a.M > 0 && a.N > 0 && a.K > 0;
@@ -431,21 +461,20 @@ int tc_error_flag(cudaStream_t st) {
   return h;
 }
 
-void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st) {
-  const bool bf16 = kind == TcKind::BF16x3;
+namespace {
+template <class CF>
+void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  constexpr int TN = CF::TN;
   const size_t esz = bf16 ? 2 : 4;
-  const size_t need = esz * ((size_t)2 * ((a.M + TM - 1) / TM * TM) * a.K +
-                             (size_t)2 * ((a.N + TN - 1) / TN * TN) * a.K);
+  // split operands are stored with their row counts rounded up to the tile (zero rows beyond
+  // M or N), so every TMA box lies inside its tensor
+  const int Mp = (a.M + TM - 1) / TM * TM, Np = (a.N + TN - 1) / TN * TN;
+  const size_t need = esz * ((size_t)2 * Mp * a.K + (size_t)2 * Np * a.K);
   if (need + 256 > scratch_bytes) throw Error(GLASSO_ERR_OOM, "tensor-core scratch too small");
   static std::once_flag once;
   std::call_once(once, [] {
-    CUDA_CHECK(cudaMalloc(&g_err, sizeof(int)));
-    CUDA_CHECK(cudaMemset(g_err, 0, sizeof(int)));
-    CUDA_CHECK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    CUDA_CHECK(cudaFuncSetAttribute(k_gemm_tc<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM_BYTES));
   });
-  // split operands are stored with their row counts rounded up to the 128-row tile (zero
-  // rows beyond M or N), so every TMA box lies inside its tensor
-  const int Mp = (a.M + TM - 1) / TM * TM, Np = (a.N + TN - 1) / TN * TN;
   uint8_t* base = static_cast<uint8_t*>(scratch);
   void* Ah = base;
   void* Al = base + esz * (size_t)Mp * a.K;
@@ -454,8 +483,10 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
   // A part: [M][K] = op(A); B part: [N][K] = op(B)^T
   split2(split_job(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, Ah, Al, a.K),
          split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K), bf16, st);
-  const CUtensorMap mAh = make_map(Ah, bf16, Mp, a.K, a.K), mAl = make_map(Al, bf16, Mp, a.K, a.K);
-  const CUtensorMap mBh = make_map(Bh, bf16, Np, a.K, a.K), mBl = make_map(Bl, bf16, Np, a.K, a.K);
+  const CUtensorMap mAh = make_map(Ah, bf16, Mp, a.K, a.K, TM, CF::KB);
+  const CUtensorMap mAl = make_map(Al, bf16, Mp, a.K, a.K, TM, CF::KB);
+  const CUtensorMap mBh = make_map(Bh, bf16, Np, a.K, a.K, TN, CF::KB);
+  const CUtensorMap mBl = make_map(Bl, bf16, Np, a.K, a.K, TN, CF::KB);
   TcArgs p;
   p.C = a.C;
   p.ldc = a.ldc;
@@ -466,14 +497,32 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
   p.beta = a.beta;
   p.lower = a.lower;
   p.krule = a.krule;
-  p.kstep = bf16 ? 64 : 32;
+  p.kstep = CF::KB / (int)esz;
   const uint32_t ab = bf16 ? 1u : 2u;  // operand format: BF16 = 1 (kind::f16), TF32 = 2 (kind::tf32)
   p.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   p.flag = a.flag;
   p.err = g_err;
   dim3 grid(((a.N + TN - 1) / TN) * ((a.M + TM - 1) / TM));
-  k_gemm_tc<<<grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
+  k_gemm_tc<CF><<<grid, CF::THREADS, CF::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
   LAUNCH_CHECK();
+}
+}  // namespace
+
+void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  static std::once_flag once;
+  static bool square = false;
+  std::call_once(once, [] {
+    CUDA_CHECK(cudaMalloc(&g_err, sizeof(int)));
+    CUDA_CHECK(cudaMemset(g_err, 0, sizeof(int)));
+    // GLASSO_TC_TILE=128 selects the 128 x 128 tiles (for comparison); 128 x 256 otherwise
+    const char* t = std::getenv("GLASSO_TC_TILE");
+    square = t && std::atoi(t) == 128;
+  });
+  const bool bf16 = kind == TcKind::BF16x3;
+  if (square)
+    tc_gemm_cfg<CfgSquare>(a, bf16, scratch, scratch_bytes, st);
+  else
+    tc_gemm_cfg<CfgWide>(a, bf16, scratch, scratch_bytes, st);
 }
 
 }  // namespace glasso

@@ -36,6 +36,18 @@ def test_status_strings_and_defaults(glasso):
     cfg = glasso.glasso_config()
     assert glasso.glasso_config_default(C.byref(cfg)) == 0
     assert cfg.max_iter == 500 and cfg.shrink == 0.5 and cfg.t_min == 1e-4 and cfg.precision == 0
+    assert cfg.products == glasso.PRODUCTS["auto"] == 0
+    # the binding's structures match the header's layout
+    assert C.sizeof(glasso.glasso_profile) == 3 * 8 * len(glasso.PROF_CLASSES)
+
+
+def test_bad_products_option_is_rejected(glasso):
+    cfg = glasso.glasso_config()
+    glasso.glasso_config_default(C.byref(cfg))
+    cfg.products = 7
+    h = C.c_void_p()
+    assert glasso.glasso_create(C.byref(cfg), C.byref(h)) == 1  # GLASSO_ERR_ARG, before any CUDA call
+    assert not h.value
 
 
 def test_argument_checks_need_no_gpu(glasso):

@@ -28,7 +28,8 @@ TOL = {"tf32x3": dict(sandwich=2e-5, chol=1e-6, logdet=1e-6),
 
 @pytest.fixture(scope="module", params=["tf32x3", "bf16x3"])
 def mixed(request, glasso):
-    h = glasso.Handle(precision=request.param)
+    # dense products: these tests are about the tensor-core path
+    h = glasso.Handle(precision=request.param, products="dense")
     yield request.param, h
     h.close()
 
@@ -106,3 +107,21 @@ def test_solve_matches_fp64_oracle(mixed, case):
     gap = abs(res["objective"] - ref["F"]) / abs(ref["F"])
     print(f"{prec} {case}: objective gap {gap:.2e}")
     assert gap <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_solve_with_sparse_sandwich_matches_fp64_oracle(glasso, prec):
+    """Split-precision factorisations with the exact FP64 sparse sandwich: same checks."""
+    p = inputs.grid_n10000(side=20, m=80, seed=4)
+    tol = 1e-7
+    with glasso.Handle(precision=prec, products="sparse") as h:
+        h.profile_start()
+        theta, res = h.solve(p.S, p.lam, tol)
+        prof = h.profile_stop()
+    assert prof["spmm"]["launches"] > 0 and "sandwich" not in prof
+    ref = pista.pista(p.S, p.lam, tol=tol)
+    assert res["status"] == 0 and abs(res["iterations"] - ref["iterations"]) <= 3
+    g = p.S - np.linalg.inv(theta)
+    r = np.sum(np.abs(pista.min_norm_subgradient(theta, g, p.lam))) / np.sum(np.abs(theta))
+    assert r <= 1.05 * tol
+    assert _rel(theta, ref["theta"]) <= 1e3 * tol

@@ -86,6 +86,42 @@ def test_sandwich(fp64, n):
     assert np.array_equal(Y, Y.T)
 
 
+@pytest.fixture(scope="module")
+def fp64_dense(glasso):
+    """An FP64 handle that forms the sandwich with dense products."""
+    h = glasso.Handle(precision="fp64", products="dense")
+    yield h
+    h.close()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sandwich_dense_and_sparse_forms(fp64, fp64_dense, n):
+    """The FP64 handle forms Theta X Theta from the CSR of Theta (auto); the dense form must give
+    the same product to FP64 rounding, and both the oracle's."""
+    A, S = _iterate_like(n, 350 + n)
+    X = pista.step_gradient(S, A, pista.inverse(A), 0.02)["X"]
+    Ys = _host(fp64.op_sandwich(_dev(A), _dev(X)))
+    Yd = _host(fp64_dense.op_sandwich(_dev(A), _dev(X)))
+    Yref = pista.step_sandwich(A, X)
+    scale = np.linalg.norm(A) ** 2 * np.linalg.norm(X) + 1e-300
+    for Y in (Ys, Yd):
+        assert np.linalg.norm(Y - Yref) <= 1e-14 * scale * max(1, n) ** 0.5
+
+
+@pytest.mark.parametrize("n", [64, 257])
+def test_sparse_sandwich_is_exact_on_a_diagonal_theta(fp64, n):
+    """Theta diagonal: the sparse form makes one rounded product per entry and step,
+    Y_ij = fl(a_i fl(a_j X_ij)) on the lower triangle (mirrored), bit for bit."""
+    rng = np.random.default_rng(n)
+    a = rng.uniform(0.5, 2.0, n)
+    X = rng.standard_normal((n, n))
+    X = X + X.T
+    Y = _host(fp64.op_sandwich(_dev(np.diag(a)), _dev(X)))
+    E = a[:, None] * (a[None, :] * X)
+    E = np.tril(E) + np.tril(E, -1).T
+    assert np.array_equal(Y, E)
+
+
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("t", [1.0, 0.25])
 def test_trial_point(fp64, n, t):

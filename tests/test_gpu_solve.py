@@ -197,7 +197,20 @@ def test_profile_accounts_kernel_classes(glasso):
         h.profile_start()
         h.solve(p.S, p.lam, 1e-6)
         prof = h.profile_stop()
-    for cls in ("sandwich", "inverse", "gradient", "trial"):
+    # the FP64 form takes the sparse sandwich on this (sparse) iterate
+    for cls in ("spmm", "inverse", "gradient", "trial"):
         assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
+    assert "sandwich" not in prof
     # factorisations run launch by launch until their CUDA graph exists, then as one replay
     assert prof["trailing"]["launches"] > 0 and prof["factor"]["launches"] > 0
+
+
+def test_profile_mixed_classes(glasso):
+    """The split-precision form also accounts its FP64 residual and the symmetrising passes."""
+    p = inputs.grid_n10000(side=12, m=30)
+    with glasso.Handle(precision="tf32x3") as h:
+        h.profile_start()
+        h.solve(p.S, p.lam, 1e-6)
+        prof = h.profile_stop()
+    for cls in ("residual", "aux", "sandwich", "inverse"):
+        assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
