@@ -246,7 +246,9 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
   Profiler::Rec rec;
   prof.begin_rec(prof_class(role), gemm_flops(a), st, rec);
   const bool mixed = cfg_.precision != GLASSO_FP64;
-  if (mixed && tc_gemm_supported(a)) {
+  if (mixed && gemm_f32_supported(a)) {
+    gemm_f32(a, st);
+  } else if (mixed && tc_gemm_supported(a)) {
     tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
             ws.tc_scratch, ws.tc_scratch_bytes, st);
   } else {
@@ -400,16 +402,18 @@ void Engine::compute_inverse(double* Li, cudaStream_t st) {
   if (cfg_.precision != GLASSO_FP64) refine_inverse(st);
 }
 
-// Mixed mode: Newton-Schulz sweeps W <- W + W R, R = I - A W formed in FP64 from the sparse
-// rows of A; the correction product runs on the tensor cores, so a sweep leaves a residual of
-// about |R|^2 + 1e-6 |R|.  Sweeps stop once the residual is (or is predicted to be) below
-// 1e-10, which keeps g = S - W, the stop test and the tier-2 log-det difference at FP64-level
-// accuracy for the decisions they feed; at most three sweeps.
+// Mixed mode: Newton-Schulz sweeps W <- W + W R, R = I - A W formed exactly in FP64 from the
+// sparse rows of A.  In exact arithmetic a sweep squares R; the correction product W R runs
+// on the tensor cores and adds about c |R| (c = 3e-5 for BF16x3, 1e-6 for TF32x3 products).
+// Sweeps stop once max |R| is measured below 1e-9, or is predicted below 1e-10 after a sweep
+// (|R|^2 + c |R|); at most three sweeps.  That keeps g = S - W, the stop test and the tier-2
+// log-det difference at FP64-level accuracy for the decisions they feed.
 void Engine::refine_inverse(cudaStream_t st) {
   const int np = ws.np;
   const int64_t ld = ws.ld;
   double* rmax = &ws.sc->aux[0];
   const double nn = (double)np * (double)np;
+  const double c = cfg_.precision == GLASSO_MIXED_BF16X3 ? 3e-5 : 1e-6;
   for (int sweep = 0; sweep < 3; ++sweep) {
     {
       // the residual is a sparse-dense product: through the CSR of A when it fits
@@ -428,7 +432,7 @@ void Engine::refine_inverse(cudaStream_t st) {
     CUDA_CHECK(cudaMemcpyAsync(&h, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
     ws.hs->aux[1 + sweep] = h;
-    if (h < 1e-10) break;
+    if (h < 1e-9) break;
     GemmArgs g = gemm_args(ws.W, ld, 0, ws.T, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
     g.lower = 1;
     gemm(g, GemmRole::Refine, st);
@@ -438,7 +442,7 @@ void Engine::refine_inverse(cudaStream_t st) {
       add_lower_mirror(ws.W, ws.Y, ld, np, st);
       prof.end_rec(rec, st);
     }
-    if (h * h + 1e-6 * h < 1e-11) break;  // the sweep just made has brought it below 1e-10
+    if (h * h + c * h < 1e-10) break;  // the sweep just made has brought it below 1e-10
   }
 }
 

@@ -294,13 +294,15 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
   const double* X22 = c.X + (int64_t)(o + s1) * ld + o + s1;
   double* X21 = c.X + (int64_t)(o + s1) * ld + o;
   // L21 = A21 X11^T (X11^T upper triangular).  The tensor-core product reads its operands
-  // from the split copies made before it starts, so it may overwrite A21 in place; the FP64
-  // kernel reads A21 tile by tile and goes through T.
-  GemmArgs a = gemm_args(A21, ld, 0, X11, ld, 1, c.fp32_leaf ? A21 : c.T, ld, s2, s1, s1, 1.0, 0.0);
+  // from the split copies made before it starts, so it may overwrite A21 in place; the
+  // CUDA-core kernels (FP64, and FP32 for small products) read A21 tile by tile and go
+  // through T.
+  const bool in_place = c.fp32_leaf && std::max(s1, s2) > kSmallGemm;
+  GemmArgs a = gemm_args(A21, ld, 0, X11, ld, 1, in_place ? A21 : c.T, ld, s2, s1, s1, 1.0, 0.0);
   a.krule = KR_HI_COL;
   a.flag = c.pd;
   (*c.gemm)(a, GemmRole::Panel, c.st);
-  if (!c.fp32_leaf) {
+  if (!in_place) {
     k_copy_block<<<std::min(s2, 1024), 256, 0, c.st>>>(c.T, A21, ld, s2, s1, c.pd);
     LAUNCH_CHECK();
   }

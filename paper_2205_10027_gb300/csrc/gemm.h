@@ -1,6 +1,7 @@
 // Dense products of the pISTA path: the argument block shared by the FP64 (CUDA-core)
 // and the split-precision tensor-core GEMMs.
 #pragma once
+#include <algorithm>
 #include "common.cuh"
 
 namespace glasso {
@@ -44,5 +45,12 @@ inline GemmArgs gemm_args(const double* A, int64_t lda, int transA, const double
 }
 
 void gemm_f64(const GemmArgs& a, int batch, cudaStream_t st);
+
+// Products with max(M, N) <= kSmallGemm run, in the split-precision modes, on the FP32
+// CUDA-core kernel (gemm_f32.cu): at that size a tensor-core product is dominated by its
+// fixed costs.  M, N multiples of 32, K of 16, C distinct from A and B.
+constexpr int kSmallGemm = 640;
+bool gemm_f32_supported(const GemmArgs& a);
+void gemm_f32(const GemmArgs& a, cudaStream_t st);
 
 }  // namespace glasso

@@ -245,17 +245,24 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   __syncthreads();
 
   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows of the tile) and the
-  // columns of its 128-column half w / 4; thread (w, l) owns row 32 (w % 4) + l
+  // columns of its 128-column half w / 4, 32 x 32 at a time; each block is transposed through
+  // shared memory (the drained operand ring) so that a warp stores 32 consecutive doubles of
+  // one row per instruction
   bool ok = !*s_abort;
   if (ok && nk > 0) ok = mbar_wait(done, 0);
   ok = __syncthreads_and(ok);  // uniform: tcgen05.ld below is warp-collective
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int wq = warp & 3;
   const int c_first = (warp >> 2) * 4, c_end = min(TN / 32, c_first + 4);
-  const int r = row0 + wq * 32 + lane;
+  float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // [32][33] per warp
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(p.err, 1);
   } else {
+    // FP32 arithmetic with integer conversions (the FP64 pipe is too narrow to spend two
+    // operations per output element); C stays FP64 in memory.  alpha and beta are 0 or +-1
+    // in every product of the solver, so only the beta != 0 update rounds, to FP32, which
+    // is the accuracy of the split products themselves.
+    const float al = (float)p.alpha, be = (float)p.beta;
 #pragma unroll 1
     for (int c = c_first; c < c_end; ++c) {
       float v[32];
@@ -265,21 +272,19 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
       }
-      if (r < p.M) {
-        // FP32 arithmetic with integer conversions (the FP64 pipe is too narrow to spend two
-        // operations per output element); C stays FP64 in memory.  alpha and beta are 0 or
-        // +-1 in every product of the solver, so only the beta != 0 update rounds, to FP32,
-        // which is the accuracy of the split products themselves.
-        double* dst = p.C + (int64_t)r * p.ldc + col0 + c * 32;
-        const float al = (float)p.alpha, be = (float)p.beta;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = col0 + c * 32 + j;
-          if (col >= p.N || (p.lower && col > r)) continue;
-          const float a = al * v[j];
-          dst[j] = f32_to_f64(p.beta == 0.0 ? a : fmaf(be, f64_to_f32(dst[j]), a));
-        }
+      for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];  // row lane, column j
+      __syncwarp();
+      const int col = col0 + c * 32 + lane;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int r = row0 + wq * 32 + rr;
+        if (r >= p.M || col >= p.N || (p.lower && col > r)) continue;
+        double* dst = p.C + (int64_t)r * p.ldc + col;
+        const float a = al * stage[rr * 33 + lane];
+        *dst = f32_to_f64(p.beta == 0.0 ? a : fmaf(be, f64_to_f32(*dst), a));
       }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

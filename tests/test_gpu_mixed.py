@@ -74,6 +74,8 @@ def test_cholesky_and_inverse(mixed, n):
     assert abs(ld - ldref) <= TOL[prec]["logdet"] * abs(ldref)
     W = h.op_inverse(_dev(A)).cpu().numpy()
     assert _rel(W, pista.inverse(A)) <= 1e-9
+    # the refinement's own stop rule, checked on the host in FP64: max |I - A W| <= 1e-9
+    assert np.max(np.abs(np.eye(n) - A @ W)) <= 1e-9
 
 
 @pytest.mark.parametrize("case", ["chain", "grid", "er"])
