@@ -405,8 +405,9 @@ void Engine::compute_inverse(double* Li, cudaStream_t st) {
 // Mixed mode: Newton-Schulz sweeps W <- W + W R, R = I - A W formed exactly in FP64 from the
 // sparse rows of A.  In exact arithmetic a sweep squares R; the correction product W R runs
 // on the tensor cores and adds about c |R| (c = 3e-5 for BF16x3, 1e-6 for TF32x3 products).
-// Sweeps stop once max |R| is measured below 1e-9, or is predicted below 1e-10 after a sweep
-// (|R|^2 + c |R|); at most three sweeps.  That keeps g = S - W, the stop test and the tier-2
+// Sweeps stop once max |R| is measured below 1e-9, or is predicted below it after a sweep
+// (|R|^2 + c |R|, with c an upper estimate of the correction product's relative error); at
+// most three sweeps.  That keeps g = S - W, the stop test and the tier-2
 // log-det difference at FP64-level accuracy for the decisions they feed.
 void Engine::refine_inverse(cudaStream_t st) {
   const int np = ws.np;
@@ -442,7 +443,7 @@ void Engine::refine_inverse(cudaStream_t st) {
       add_lower_mirror(ws.W, ws.Y, ld, np, st);
       prof.end_rec(rec, st);
     }
-    if (h * h + c * h < 1e-10) break;  // the sweep just made has brought it below 1e-10
+    if (h * h + c * h < 1e-9) break;  // the sweep just made has brought it below 1e-9
   }
 }
 

@@ -46,10 +46,10 @@ inline GemmArgs gemm_args(const double* A, int64_t lda, int transA, const double
 
 void gemm_f64(const GemmArgs& a, int batch, cudaStream_t st);
 
-// Products with max(M, N) <= kSmallGemm run, in the split-precision modes, on the FP32
-// CUDA-core kernel (gemm_f32.cu): at that size a tensor-core product is dominated by its
-// fixed costs.  M, N multiples of 32, K of 16, C distinct from A and B.
-constexpr int kSmallGemm = 640;
+// Products with max(M, N) <= kSmallGemm and K <= 256 run, in the split-precision modes, on
+// the FP32 CUDA-core kernel (gemm_f32.cu): at that size a tensor-core product is dominated by
+// its fixed costs.  M, N multiples of 64, C distinct from A and B.
+constexpr int kSmallGemm = 256;
 bool gemm_f32_supported(const GemmArgs& a);
 void gemm_f32(const GemmArgs& a, cudaStream_t st);
 

@@ -1,81 +1,109 @@
 // Small dense products of the split-precision modes on the CUDA cores in FP32 arithmetic.
 //
-// The recursive factorisation issues hundreds of products with M, N <= 640 (its lowest
+// The recursive factorisation issues hundreds of products with M, N, K <= 256 (its lowest
 // levels); a tensor-core product of that size is dominated by fixed costs (operand split
 // launch, TMEM allocation, pipeline fill, epilogue), while the CUDA cores finish it in a few
 // microseconds.  FP64 operands are converted to FP32 when staged in shared memory (integer
 // conversion), products accumulate in FP32 - the accuracy of the split products they
 // replace - and the result is stored in FP64.  Same structure options as the other GEMMs
 // (transposes, lower-triangle output, k-ranges of triangular operands, failure flag).
+#include <mutex>
 #include "gemm.h"
 
 namespace glasso {
 
 namespace {
-// TILE x TILE output per block, BK = 16, 256 threads with (TILE / 16)^2 outputs each.
-template <int TILE>
-__global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmArgs p) {
-  constexpr int BK = 16, R = TILE / 16;
-  if (p.flag && *p.flag == 0) return;
-  const int tm = blockIdx.y, tn = blockIdx.x;
-  const int row0 = tm * TILE, col0 = tn * TILE;
-  if (p.lower && row0 + TILE <= col0) return;
-  const double* __restrict__ A = p.A;
-  const double* __restrict__ B = p.B;
-  double* __restrict__ C = p.C;
+constexpr int TILE = 32;          // output tile per block (small tiles: many blocks per product)
+constexpr int KMAX = 256;         // largest k-range staged at once
 
+// Stage rows [r0, r0 + TILE) x k-range [k_lo, k_lo + kn) of an operand into S[r][k] (pitch
+// kp), converting to FP32.  KFAST: the operand is stored as G[r][k] (k contiguous); else as
+// G[k][r] (r contiguous).  Each thread issues its loads in batches of 16 or 32 independent
+// ones before converting any, so a block keeps its whole tile in flight.
+template <bool KFAST>
+__device__ __forceinline__ void stage_operand(const double* __restrict__ G, int64_t ld, int r0, int k_lo, int kn,
+                                              float* S, int kp, int warp, int lane) {
+  if (KFAST) {
+    // warp w: rows w + 8 i (i < 4); lanes: k = lane + 32 q (q < 8 covers kn <= 256)
+    double v[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = warp + 8 * i, k = lane + 32 * q;
+        v[i][q] = k < kn ? G[(int64_t)(r0 + r) * ld + k_lo + k] : 0.0;
+      }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = warp + 8 * i, k = lane + 32 * q;
+        if (k < kn) S[r * kp + k] = f64_to_f32(v[i][q]);
+      }
+  } else {
+    // warp w: k = k0 + w + 8 i (i < 16); lanes: r = lane
+    for (int k0 = 0; k0 < kn; k0 += 128) {
+      double v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = k0 + warp + 8 * i;
+        v[i] = k < kn ? G[(int64_t)(k_lo + k) * ld + r0 + lane] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = k0 + warp + 8 * i;
+        if (k < kn) S[lane * kp + k] = f64_to_f32(v[i]);
+      }
+    }
+  }
+}
+
+// One TILE x TILE output tile per block, 256 threads with 2 x 2 outputs each (rows ty + 16 i,
+// columns tx + 16 j).  The tile's whole k-range of op(A) and op(B) is staged at once in
+// shared memory as As[m][k] and Bs[n][k] (row pitch kn + 1, odd, so that both the staging
+// stores and the strided reads hit distinct banks): a product this small is latency-bound,
+// so every global load of the block is issued before the first multiply.
+__global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmArgs p) {
+  if (p.flag && *p.flag == 0) return;
+  const int row0 = blockIdx.y * TILE, col0 = blockIdx.x * TILE;
+  if (p.lower && row0 + TILE <= col0) return;
   int k_lo = 0, k_hi = p.K;
   if (p.krule == KR_LO_COL) k_lo = col0;
   else if (p.krule == KR_LO_ROW) k_lo = row0;
   else if (p.krule == KR_HI_ROW) k_hi = min(p.K, row0 + TILE);
   else if (p.krule == KR_HI_COL) k_hi = min(p.K, col0 + TILE);
-  k_lo = k_lo / BK * BK;
-
-  __shared__ float As[BK][TILE + 1];
-  __shared__ float Bs[BK][TILE + 1];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int kn = max(k_hi - k_lo, 0), kp = kn + 1;
+  extern __shared__ float sm[];
+  float* As = sm;              // [TILE][kp]: As[m][k] = op(A)[row0 + m][k_lo + k]
+  float* Bs = sm + TILE * kp;  // [TILE][kp]: Bs[n][k] = op(B)[k_lo + k][col0 + n]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // op(A)[m][k] is A[m][k] (k contiguous) or A[k][m]; op(B)[k][n] is B[n][k] or B[k][n]
+  if (!p.transA) stage_operand<true>(p.A, p.lda, row0, k_lo, kn, As, kp, warp, lane);
+  else stage_operand<false>(p.A, p.lda, row0, k_lo, kn, As, kp, warp, lane);
+  if (p.transB) stage_operand<true>(p.B, p.ldb, col0, k_lo, kn, Bs, kp, warp, lane);
+  else stage_operand<false>(p.B, p.ldb, col0, k_lo, kn, Bs, kp, warp, lane);
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  constexpr int R = TILE / 16;
   float acc[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = 0.f;
-
-  for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
-    // stage op(A)[row0 .. + TILE, k0 .. + 16] as As[k][m] and op(B)[k0 .., col0 ..] as Bs[k][n]
+  const float* a0 = As + ty * kp;
+  const float* b0 = Bs + tx * kp;
+#pragma unroll 4
+  for (int k = 0; k < kn; ++k) {
+    float a[R], b[R];
 #pragma unroll
-    for (int r = 0; r < (TILE * BK) / 256; ++r) {
-      const int e = tid + r * 256;
-      if (!p.transA) {
-        const int m = e >> 4, k = e & 15;  // 16 consecutive k of one row per 16 threads
-        As[k][m] = f64_to_f32(A[(int64_t)(row0 + m) * p.lda + (k0 + k)]);
-      } else {
-        const int k = e / TILE, m = e % TILE;  // op(A)[m][k] = A[k][m]: contiguous in m
-        As[k][m] = f64_to_f32(A[(int64_t)(k0 + k) * p.lda + (row0 + m)]);
-      }
-      if (!p.transB) {
-        const int k = e / TILE, n = e % TILE;
-        Bs[k][n] = f64_to_f32(B[(int64_t)(k0 + k) * p.ldb + (col0 + n)]);
-      } else {
-        const int n = e >> 4, k = e & 15;  // op(B)[k][n] = B[n][k]
-        Bs[k][n] = f64_to_f32(B[(int64_t)(col0 + n) * p.ldb + (k0 + k)]);
-      }
-    }
-    __syncthreads();
+    for (int i = 0; i < R; ++i) a[i] = a0[16 * i * kp + k];
 #pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      float a[R], b[R];
+    for (int j = 0; j < R; ++j) b[j] = b0[16 * j * kp + k];
 #pragma unroll
-      for (int i = 0; i < R; ++i) a[i] = As[k][ty + 16 * i];
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < R; ++j) b[j] = Bs[k][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < R; ++i)
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+      for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
-
   const float al = (float)p.alpha, be = (float)p.beta;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -84,26 +112,28 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmAr
     for (int j = 0; j < R; ++j) {
       const int c = col0 + tx + 16 * j;
       if (p.lower && c > r) continue;
-      double* dst = C + (int64_t)r * p.ldc + c;
+      double* dst = p.C + (int64_t)r * p.ldc + c;
       const float v = al * acc[i][j];
       *dst = f32_to_f64(p.beta == 0.0 ? v : fmaf(be, f64_to_f32(*dst), v));
     }
   }
 }
+
+constexpr size_t smem_for(int K) { return (size_t)2 * TILE * (K + 1) * sizeof(float); }
 }  // namespace
 
 bool gemm_f32_supported(const GemmArgs& a) {
-  return a.M > 0 && a.N > 0 && a.K > 0 && a.M % 32 == 0 && a.N % 32 == 0 && a.K % 16 == 0 &&
+  return a.M > 0 && a.N > 0 && a.K > 0 && a.M % TILE == 0 && a.N % TILE == 0 && a.K <= KMAX &&
          std::max(a.M, a.N) <= kSmallGemm && a.C != a.A && a.C != a.B;
 }
 
 void gemm_f32(const GemmArgs& a, cudaStream_t st) {
   if (!gemm_f32_supported(a)) throw Error(1, "gemm_f32: unsupported shape or in-place product");
-  if (a.M % 64 == 0 && a.N % 64 == 0 && (int64_t)a.M * a.N >= 256 * 256) {
-    k_gemm_f32<64><<<dim3(a.N / 64, a.M / 64), 256, 0, st>>>(a);
-  } else {
-    k_gemm_f32<32><<<dim3(a.N / 32, a.M / 32), 256, 0, st>>>(a);
-  }
+  static std::once_flag once;
+  std::call_once(once, [] {
+    CUDA_CHECK(cudaFuncSetAttribute(k_gemm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(KMAX)));
+  });
+  k_gemm_f32<<<dim3(a.N / TILE, a.M / TILE), 256, smem_for(a.K), st>>>(a);
   LAUNCH_CHECK();
 }
 
