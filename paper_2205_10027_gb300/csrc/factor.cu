@@ -110,10 +110,25 @@ __global__ void __launch_bounds__(PT) k_leaf_chol_inv(double* Ablk, int64_t ld, 
   __shared__ double red[32];
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < NB * NB; e += PT) {
-    const int i = e / NB, c = e % NB;
-    a[i * LDS + c] = (c <= i) ? from_f64<T>(Ablk[(int64_t)i * ld + c]) : T(0);
-    x[i * LDS + c] = T(0);
+  {
+    // every thread issues all of its loads (lower triangle only) before converting any
+    constexpr int PER = NB * NB / PT, BATCH = PER < 16 ? PER : 16;
+    static_assert(NB * NB % PT == 0 && PER % BATCH == 0, "load split");
+#pragma unroll
+    for (int u0 = 0; u0 < PER; u0 += BATCH) {
+      double v[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = tid + (u0 + u) * PT, i = e / NB, c = e % NB;
+        v[u] = (c <= i) ? Ablk[(int64_t)i * ld + c] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = tid + (u0 + u) * PT, i = e / NB, c = e % NB;
+        a[i * LDS + c] = from_f64<T>(v[u]);
+        x[i * LDS + c] = T(0);
+      }
+    }
   }
   if (tid == 0) fail = 0;
   __syncthreads();
