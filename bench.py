@@ -34,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pISTA iters/s (n=10k grid, lambda=0.1); time-to-KKT 1e-6"
+
+# DRAM bytes (read + write) per launch of the tensor-core product in the step (the W = X^T X
+# and W R launches whose CUDA-event times give the roofline), from one ncu capture of this
+# workload (profiles/k_gemm_tc_step_traffic_n10000.md); BF16x3 only, None elsewhere.
+TC_TRAFFIC_PER_LAUNCH = {"bf16x3": 2.126e9}
 UNIT = "iters/s"
 
 
@@ -283,7 +288,8 @@ def run_ours(args):
             peak = peaks.get("bf16_tflops_sustained", 1700.0) * ratio / 3.0
             bound, kernel = "tensor", "k_gemm_tc"
         rl = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-              "frac": achieved / peak if peak else None, "traffic": None,
+              "frac": achieved / peak if peak else None,
+              "traffic": TC_TRAFFIC_PER_LAUNCH.get(args.precision) if args.side == 100 and args.m == 2000 else None,
               "peak_source": peak_kind if args.precision == "fp64" else f"{peak_kind} bf16 sustained x nominal dtype ratio / 3 split products",
               "launches": g_launch, "share_of_step": g_ms / ms if ms else None}
         if "factor" in prof and prof["factor"]["ms"]:
