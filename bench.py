@@ -520,7 +520,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--batch-max-iter", type=int, default=500)
-    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--served", type=int, default=0, help="served stream of this many requests")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--served-nmax", type=int, default=4096)

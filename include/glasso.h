@@ -49,8 +49,10 @@ typedef enum {
 
 typedef enum {
   GLASSO_FP64 = 0,          /* every step in FP64 */
-  GLASSO_MIXED_TF32X3 = 1,  /* dense products on the tensor cores with 3-term TF32 splits;
-                               FP64 Cholesky panels, FP64-refined W, FP64 decisions */
+  GLASSO_MIXED_TF32X3 = 1,  /* dense products wider than 256 on the tensor cores with
+                               3-term TF32 splits, smaller ones and the 128 x 128 Cholesky
+                               leaves in FP32 arithmetic; FP64 storage, W refined to FP64
+                               accuracy, FP64 line-search and stop decisions */
   GLASSO_MIXED_BF16X3 = 2   /* as GLASSO_MIXED_TF32X3 with 3-term BF16 splits */
 } glasso_precision;
 

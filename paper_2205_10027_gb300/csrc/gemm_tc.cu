@@ -50,6 +50,7 @@ struct TcArgs {
   double alpha, beta;
   int lower, krule;
   int kstep;          // K elements per stage: KB / element size
+  int group_m;        // tile rows per group of the tile order
   uint32_t idesc;     // tcgen05 instruction descriptor
   const int* flag;
   int* err;
@@ -154,10 +155,10 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   // grouped tile order: consecutive blocks walk down a column of GROUP_M tiles, so the
   // CTAs resident at one time cover a near-square patch and share operand panels in L2
   const int tiles_m = (p.M + TM - 1) / TM, tiles_n = (p.N + TN - 1) / TN;
-  const int per_group = GROUP_M * tiles_n;
+  const int per_group = p.group_m * tiles_n;
   const int b = blockIdx.x;
-  const int first_m = (b / per_group) * GROUP_M;
-  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int first_m = (b / per_group) * p.group_m;
+  const int gm = min(p.group_m, tiles_m - first_m);
   const int tm = first_m + (b % per_group) % gm, tn = (b % per_group) / gm;
   const int row0 = tm * TM, col0 = tn * TN;
   if (p.lower && row0 + TM <= col0) return;  // tile entirely above the diagonal
@@ -434,8 +435,9 @@ SplitJob split_job(const double* src, int64_t lds, int rows, int rows_out, int c
   return SplitJob{src, lds, rows, rows_out, cols, trans ? 1 : 0, hi, lo, ldo, (cols + 31) / 32};
 }
 
-void split2(const SplitJob& a, const SplitJob& b, bool bf16, cudaStream_t st) {
-  dim3 grid(std::max(a.tiles_x, b.tiles_x), (std::max(a.rows_out, b.rows_out) + 31) / 32, 2);
+// Both jobs in one launch; jobs == 1 runs only the first.
+void split2(const SplitJob& a, const SplitJob& b, bool bf16, cudaStream_t st, int jobs = 2) {
+  dim3 grid(std::max(a.tiles_x, b.tiles_x), (std::max(a.rows_out, b.rows_out) + 31) / 32, jobs);
   if (bf16)
     k_split<true><<<grid, dim3(32, 8), 0, st>>>(a, b);
   else
@@ -485,9 +487,19 @@ void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_byt
   void* Al = base + esz * (size_t)Mp * a.K;
   void* Bh = base + esz * (size_t)2 * Mp * a.K;
   void* Bl = base + esz * ((size_t)2 * Mp * a.K + (size_t)Np * a.K);
-  // A part: [M][K] = op(A); B part: [N][K] = op(B)^T
-  split2(split_job(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, Ah, Al, a.K),
-         split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K), bf16, st);
+  // A part: [M][K] = op(A); B part: [N][K] = op(B)^T.  When they are the same matrix (the
+  // symmetric products op(A) op(A)^T of the trailing updates and of W = X^T X) it is split
+  // once, with the B part's row padding, and both maps read it.
+  const bool same = a.A == a.B && a.lda == a.ldb && (a.transA != 0) == (a.transB == 0) && a.M == a.N;
+  if (same) {
+    split2(split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K),
+           split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K), bf16, st, 1);
+    Ah = Bh;
+    Al = Bl;
+  } else {
+    split2(split_job(a.A, a.lda, a.M, Mp, a.K, a.transA != 0, Ah, Al, a.K),
+           split_job(a.B, a.ldb, a.N, Np, a.K, a.transB == 0, Bh, Bl, a.K), bf16, st);
+  }
   const CUtensorMap mAh = make_map(Ah, bf16, Mp, a.K, a.K, TM, CF::KB);
   const CUtensorMap mAl = make_map(Al, bf16, Mp, a.K, a.K, TM, CF::KB);
   const CUtensorMap mBh = make_map(Bh, bf16, Np, a.K, a.K, TN, CF::KB);
@@ -503,6 +515,7 @@ void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_byt
   p.lower = a.lower;
   p.krule = a.krule;
   p.kstep = CF::KB / (int)esz;
+  p.group_m = GROUP_M;
   const uint32_t ab = bf16 ? 1u : 2u;  // operand format: BF16 = 1 (kind::f16), TF32 = 2 (kind::tf32)
   p.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   p.flag = a.flag;
