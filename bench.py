@@ -38,7 +38,7 @@ METRIC = "pISTA iters/s (n=10k grid, lambda=0.1); time-to-KKT 1e-6"
 # DRAM bytes (read + write) per launch of the tensor-core product in the step (the W = X^T X
 # and W R launches whose CUDA-event times give the roofline), from one ncu capture of this
 # workload (profiles/k_gemm_tc_step_traffic_n10000.md); BF16x3 only, None elsewhere.
-TC_TRAFFIC_PER_LAUNCH = {"bf16x3": 2.126e9}
+TC_TRAFFIC_PER_LAUNCH = {"bf16x3": 2.015e9}
 UNIT = "iters/s"
 
 
