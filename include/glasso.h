@@ -238,7 +238,8 @@ glasso_status glasso_op_cholesky(glasso_handle* h, const double* A, int64_t n, d
                                  int32_t* pd, double* logdet);
 
 /* W = A^{-1} (eq. grad_hessian needs it) for a symmetric positive-definite A, from the
- * Cholesky factor: W = L^{-T} L^{-1}.  GLASSO_ERR_NOT_PD if A is not PD. */
+ * Cholesky factor: W = L^{-T} L^{-1}.  In the split-precision modes W is refined until
+ * max |I - A W| <= 1e-9 (measured or predicted).  GLASSO_ERR_NOT_PD if A is not PD. */
 glasso_status glasso_op_inverse(glasso_handle* h, const double* A, int64_t n, double* W);
 
 /* From (S, A, W = A^{-1}): g = S - W (eq. grad_hessian), free set M (eqs. free_set, M),
@@ -248,7 +249,8 @@ glasso_status glasso_op_gradient(glasso_handle* h, const double* S, const double
                                  const double* W, int64_t n, double lambda, double* X,
                                  int8_t* code, double sums[4]);
 
-/* Y = A X A for symmetric A, X (the two triple products of eq. b, fused). */
+/* Y = A X A for symmetric A, X (the two products of eq. b), formed as the handle's
+ * glasso_config.products says: from the CSR of A in FP64, or by two dense products. */
 glasso_status glasso_op_sandwich(glasso_handle* h, const double* A, const double* X, int64_t n,
                                  double* Y);
 
