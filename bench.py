@@ -380,25 +380,27 @@ def run_paper_table(args):
     standardised), solved end to end from host S through glasso_solve, beside the printed
     GPU numbers of Table 1 or 2."""
     import torch
-    from paper_2205_10027_gb300 import binding, inputs
+    from paper_2205_10027_gb300 import binding, inputs, metrics
     tab = PAPER_TABLES[args.paper_table]
     n = tab["n"]
     seeds = args.paper_seeds
     h = binding.Handle(precision=args.precision, max_iter=1000)
     rows = []
     for kind, alpha, paper_s, paper_it in tab["rows"]:
-        times, its, nnz = [], [], []
+        times, its, nnz, mcc = [], [], [], []
         for rep in range(seeds):
-            S = inputs.paper_protocol(kind, n, seed=300 + rep)
+            S, T = inputs.paper_protocol(kind, n, seed=300 + rep, return_theta=True)
             h.solve(S, alpha, 1e-2) if rep == 0 else None   # warm the workspace and graphs
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, res = h.solve(S, alpha, 1e-2)
+            theta, res = h.solve(S, alpha, 1e-2)
             times.append(time.perf_counter() - t0)
             its.append(res["iterations"])
             nnz.append(res["nnz"])
+            mcc.append(metrics.support_mcc(T, theta))
         rows.append({"kind": kind, "alpha": alpha, "seconds": statistics.mean(times),
                      "iterations": statistics.mean(its), "nnz": statistics.mean(nnz),
+                     "mcc": statistics.mean(mcc),
                      "paper_seconds": paper_s, "paper_iterations": paper_it,
                      "speedup_vs_paper": paper_s / statistics.mean(times)})
     h.close()

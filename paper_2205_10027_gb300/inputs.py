@@ -203,10 +203,13 @@ def paper_theta(kind: str, n: int, rng: np.random.Generator) -> np.ndarray:
     raise ValueError(kind)
 
 
-def paper_protocol(kind: str, n: int, seed: int, m_frac: float = 0.03) -> np.ndarray:
+def paper_protocol(kind: str, n: int, seed: int, m_frac: float = 0.03, return_theta: bool = False):
+    """S of the paper's synthetic protocol (standardised samples); with return_theta, also
+    the ground-truth precision matrix it was sampled from."""
     rng = np.random.default_rng(seed)
     T = paper_theta(kind, n, rng)
     S = sample_covariance(T, max(2, int(round(m_frac * n))), rng)
     d = 1.0 / np.sqrt(np.diag(S))
     S = S * d[:, None] * d[None, :]
-    return 0.5 * (S + S.T)
+    S = 0.5 * (S + S.T)
+    return (S, T) if return_theta else S
