@@ -185,7 +185,7 @@ def run_ours(args):
     S_dev = torch.from_numpy(np.ascontiguousarray(p.S)).to(dev)
     stream = torch.cuda.current_stream(dev)
     h = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
-                       products=args.products)
+                       products=args.products, method=args.method)
 
     def barrier():
         if world > 1:
@@ -220,7 +220,7 @@ def run_ours(args):
     S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
     out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
     he = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
-                        max_iter=args.steps, products=args.products)
+                        max_iter=args.steps, products=args.products, method=args.method)
     he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())  # warm the workspace
     barrier()
     t0 = time.perf_counter()
@@ -234,7 +234,7 @@ def run_ours(args):
     ttt = None
     if args.time_to_tol:
         ht = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream, max_iter=2000,
-                            products=args.products)
+                            products=args.products, method=args.method)
         barrier()
         t0 = time.perf_counter()
         _, rt = ht.solve(S_dev, p.lam, p.tol)
@@ -315,7 +315,7 @@ def run_ours(args):
             "dtype": {"fp64": "f64", "tf32x3": "f64+tf32x3", "bf16x3": "f64+bf16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"grid{args.side}x{args.side}_n{n}_m{args.m}_lam0.1",
-                       "precision": args.precision, "products": args.products,
+                       "precision": args.precision, "products": args.products, "method": args.method,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (each n x n FP64 matrix is %.0f MB)" % (8 * n * n / 1e6)},
             "gpu_launches": launches, "trials_in_timed_steps": trials,
@@ -502,6 +502,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="bf16x3")
+    ap.add_argument("--method", choices=["pista", "gista"], default="pista",
+                    help="outer method (glasso_method): Algorithm 1, or plain proximal gradient")
     ap.add_argument("--products", choices=["auto", "dense", "sparse"], default="auto",
                     help="how the sandwich products are formed (glasso_products)")
     ap.add_argument("--side", type=int, default=100)

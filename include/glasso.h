@@ -66,6 +66,14 @@ typedef enum { GLASSO_HOST = 0, GLASSO_DEVICE = 1 } glasso_memory;
  * nnz(Theta) <= n max(16, n / 256), where it also costs less than the dense products. */
 typedef enum { GLASSO_PRODUCTS_AUTO = 0, GLASSO_PRODUCTS_DENSE = 1, GLASSO_PRODUCTS_SPARSE = 2 } glasso_products;
 
+/* The outer method.  PISTA: Algorithm 1 (the default).  GISTA: the plain proximal gradient
+ * method, eq. proximal_gen with H = I (Sec. 2.2): Theta <- ST(Theta - t g, t lambda), t
+ * chosen by halving from twice the last step until the candidate is PD and satisfies the
+ * sufficient-decrease bound f(Theta_t) <= f(Theta) + <g, D> + ||D||_F^2 / (2t), never below
+ * t_safe = lambda_min(Theta)^2 / 2 (at which the gradient is Lipschitz with constant at
+ * most 1/lambda_min^2 near Theta, the bound behind Lemma 5.2); the same stop rule. */
+typedef enum { GLASSO_METHOD_PISTA = 0, GLASSO_METHOD_GISTA = 1 } glasso_method;
+
 typedef struct glasso_handle glasso_handle;
 
 typedef struct {
@@ -78,6 +86,7 @@ typedef struct {
   size_t hbm_budget_bytes;  /* device memory the handle may hold; 0 = no limit */
   int serve_slots;          /* requests the serving loop runs at once; default 8 */
   int products;             /* glasso_products: how the sandwich products of eq. b are formed */
+  int method;               /* glasso_method; default GLASSO_METHOD_PISTA */
 } glasso_config;
 
 typedef struct {

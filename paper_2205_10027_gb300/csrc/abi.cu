@@ -70,6 +70,7 @@ glasso_status glasso_config_default(glasso_config* cfg) {
   cfg->hbm_budget_bytes = 0;
   cfg->serve_slots = 8;
   cfg->products = GLASSO_PRODUCTS_AUTO;
+  cfg->method = GLASSO_METHOD_PISTA;
   return GLASSO_OK;
 }
 
@@ -81,6 +82,7 @@ glasso_status glasso_create(const glasso_config* cfg_in, glasso_handle** out) {
   if (cfg.precision < GLASSO_FP64 || cfg.precision > GLASSO_MIXED_BF16X3) return GLASSO_ERR_ARG;
   if (cfg.serve_slots <= 0) cfg.serve_slots = 8;
   if (cfg.products < GLASSO_PRODUCTS_AUTO || cfg.products > GLASSO_PRODUCTS_SPARSE) return GLASSO_ERR_ARG;
+  if (cfg.method != GLASSO_METHOD_PISTA && cfg.method != GLASSO_METHOD_GISTA) return GLASSO_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();

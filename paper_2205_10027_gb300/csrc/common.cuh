@@ -27,6 +27,7 @@ struct Scalars {
   double tr_e, tr_e2;                  // second-order log-det difference (tier 2)
   double trsa, l1;                     // objective pieces of a given matrix
   double aux[8];
+  double gista[5];                     // G-ISTA trial: tr(S At), ||At||_1, nnz(At), <g, D>, ||D||_F^2
 };
 
 // Deterministic block reduction: every block writes its partial sums; one block then

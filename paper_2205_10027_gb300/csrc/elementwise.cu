@@ -219,6 +219,73 @@ __global__ void __launch_bounds__(RT) k_trial(const double* __restrict__ A,
   }
 }
 
+// ---- G-ISTA candidate (Sec. 2.2 with H = I): At = ST(A - t g, t lam) with g = S - W, on
+//      32 x 32 tile pairs like k_trial (lower computed, mirrored; Lt = lower of At; identity
+//      padding), and partial sums of tr(S At), ||At||_1, nnz(At), <g, At - A>, ||At - A||_F^2
+__global__ void __launch_bounds__(RT) k_gista_trial(const double* __restrict__ A,
+                                                    const double* __restrict__ W,
+                                                    const double* __restrict__ S, int64_t ld,
+                                                    int64_t n, int np, double lam, double t,
+                                                    double* __restrict__ At, double* __restrict__ Lt,
+                                                    double* __restrict__ parts) {
+  __shared__ double tile[32][33];
+  __shared__ double red[32];
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  double s_tr = 0.0, s_l1 = 0.0, s_nz = 0.0, s_gd = 0.0, s_dd = 0.0;
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int bi, bj;
+    tri_tile(tt, bi, bj);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+      double at;
+      if (i < n && j < n) {
+        const double a = A[i * ld + j], s = S[i * ld + j];
+        const double g = s - W[i * ld + j];
+        at = soft_threshold(a - t * g, t * lam);
+        if (j <= i) {
+          const double w = (i == j) ? 1.0 : 2.0, d = at - a;
+          s_tr += w * s * at;
+          s_l1 += w * fabs(at);
+          s_nz += nonzero(at) ? w : 0.0;
+          s_gd += w * g * d;
+          s_dd += w * d * d;
+        }
+      } else {
+        at = (i == j) ? 1.0 : 0.0;  // identity padding
+      }
+      tile[r][tx] = at;
+      if (j <= i) {
+        At[i * ld + j] = at;
+        Lt[i * ld + j] = at;
+      }
+    }
+    __syncthreads();
+    if (bi != bj) {
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t i = (int64_t)bj * 32 + r, j = (int64_t)bi * 32 + tx;
+        At[i * ld + j] = tile[tx][r];
+      }
+    } else {
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
+        if (j > i) At[i * ld + j] = tile[tx][r];
+      }
+    }
+  }
+  const double v0 = block_sum(s_tr, red);
+  const double v1 = block_sum(s_l1, red);
+  const double v2 = block_sum(s_nz, red);
+  const double v3 = block_sum(s_gd, red);
+  const double v4 = block_sum(s_dd, red);
+  if (threadIdx.x == 0) {
+    double* p = parts + (int64_t)blockIdx.x * 5;
+    p[0] = v0; p[1] = v1; p[2] = v2; p[3] = v3; p[4] = v4;
+  }
+}
+
 // ---- tr(S A) and ||A||_1 of a full matrix
 __global__ void __launch_bounds__(RT) k_objective_terms(const double* __restrict__ S,
                                                         const double* __restrict__ A, int64_t ld,
@@ -432,6 +499,18 @@ void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, co
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int g = (int)std::min<int64_t>(ntiles, kRedBlocks);
   k_trial<<<g, RT, 0, st>>>(A, Y, code, ldc, S, ld, n, np, lam, t, At, Lt, parts);
+  LAUNCH_CHECK();
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 5, out5);
+  LAUNCH_CHECK();
+}
+
+void gista_trial(const double* A, const double* W, const double* S, int64_t ld, int64_t n, int np,
+                 double lam, double t, double* At, double* Lt, double* parts, double* out5,
+                 cudaStream_t st) {
+  const int nt = np / 32;
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+  const int g = (int)std::min<int64_t>(ntiles, kRedBlocks);
+  k_gista_trial<<<g, RT, 0, st>>>(A, W, S, ld, n, np, lam, t, At, Lt, parts);
   LAUNCH_CHECK();
   k_finalize<<<1, RT, 0, st>>>(parts, g, 5, out5);
   LAUNCH_CHECK();

@@ -23,6 +23,12 @@ void gradient(const double* S, const double* W, const double* A, int64_t ld, int
 void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, const double* S,
            int64_t ld, int64_t n, int np, double lam, double t, double* At, double* Lt,
            double* parts, double* out5, cudaStream_t st);
+// G-ISTA candidate (proximal gradient with H = I): At (full) = ST(A - t (S - W), t lam) on
+// the n x n block (identity padding), Lt (lower) = At, and out5 = {tr(S At), ||At||_1,
+// nnz(At), <S - W, At - A>, ||At - A||_F^2}.
+void gista_trial(const double* A, const double* W, const double* S, int64_t ld, int64_t n, int np,
+                 double lam, double t, double* At, double* Lt, double* parts, double* out5,
+                 cudaStream_t st);
 // out2 = {tr(S A), ||A||_1}.
 void objective_terms(const double* S, const double* A, int64_t ld, int64_t n, double* parts,
                      double* out2, cudaStream_t st);

@@ -564,8 +564,83 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   st_.F = -st_.ld_A + st_.trsa + lam * st_.l1;
 }
 
+// One iteration of the plain proximal gradient method (glasso_method GISTA; Sec. 2.2, H = I):
+// the gradient and stop test as in pISTA, then candidates ST(A - t g, t lam) from
+// t = min(1, max(2 t_last, t_safe)), halved until the candidate is PD and
+// f(At) <= f(A) + <g, D> + ||D||^2 / (2t) (f = -log det + tr(S .)), but not below
+// t_safe = lambda_min(A)^2 / 2 = 1 / (2 lambda_max(W)^2); if no candidate above t_safe
+// passes, the step is t_safe, halved further only while the candidate is not PD.
+int Engine::gista_step(double tol, int max_iter, bool keep_trace) {
+  cudaStream_t st = stream_;
+  const int np = ws.np;
+  const int64_t ld = ws.ld, n = st_.n;
+  const double lam = st_.lam;
+  Scalars& h = *ws.hs;
+  SolveOut& out = st_.out;
+  csr_valid_ = false;
+  compute_inverse(ws.Li, st);
+  {
+    Profiler::Rec rec;
+    prof.begin_rec(GLASSO_PROF_GRADIENT, 33.0 * (double)n * (double)n, st, rec);
+    gradient(ws.S, ws.W, ws.A, ld, n, lam, ws.X, ws.code, ld, ws.parts, &ws.sc->z_l1, st);
+    prof.end_rec(rec, st);
+  }
+  sync_scalars();
+  out.r = h.z_l1 / h.a_l1;
+  out.z_fro = std::sqrt(h.z_fro2);
+  out.nnz = h.nnz;
+  if (out.r <= tol) return GLASSO_OK;
+  if (st_.k >= max_iter) return GLASSO_MAX_ITER;
+  const double lmax_w = power_lambda_max(ws.W, st);
+  const double t_safe = 0.5 / (lmax_w * lmax_w);
+  const double f = -st_.ld_A + st_.trsa;
+  double t = std::min(1.0, std::max(2.0 * st_.t_last, t_safe));
+  int trials = 0;
+  bool accepted = false;
+  auto candidate = [&](double tt) -> bool {  // PD
+    {
+      Profiler::Rec rec;
+      prof.begin_rec(GLASSO_PROF_TRIAL, 32.0 * (double)n * (double)n, st, rec);
+      gista_trial(ws.A, ws.W, ws.S, ld, n, np, lam, tt, ws.At, ws.Lt, ws.parts, ws.sc->gista, st);
+      prof.end_rec(rec, st);
+    }
+    factor(ws.Lt, ws.Lti, st);
+    sync_scalars();
+    ++trials;
+    return h.pd_t != 0;
+  };
+  while (t > t_safe) {
+    if (candidate(t)) {
+      const double fn = -h.logdet_t + h.gista[0];
+      if (fn <= f + h.gista[3] + h.gista[4] / (2.0 * t)) { accepted = true; break; }
+    }
+    t *= 0.5;
+  }
+  if (!accepted) {
+    t = t_safe;
+    while (t > 1e-300) {
+      if (candidate(t)) { accepted = true; break; }
+      t *= 0.5;
+    }
+  }
+  out.trials += trials;
+  if (keep_trace) out.trace.push_back(IterRecord{st_.k, trials, 1, st_.F, out.r, out.z_fro, out.nnz, t, 0.0});
+  if (!accepted) return GLASSO_LINESEARCH_STALL;
+  std::swap(ws.A, ws.At);
+  std::swap(ws.L, ws.Lt);
+  std::swap(ws.Li, ws.Lti);
+  st_.ld_A = h.logdet_t;
+  st_.trsa = h.gista[0];
+  st_.l1 = h.gista[1];
+  st_.F = -st_.ld_A + st_.trsa + lam * st_.l1;
+  st_.t_last = t;
+  ++st_.k;
+  return -1;
+}
+
 int Engine::step(double tol, int max_iter, bool keep_trace) {
   if (!st_.active) throw Error(GLASSO_ERR_ARG, "no solve in progress (call glasso_begin)");
+  if (cfg_.method == GLASSO_METHOD_GISTA) return gista_step(tol, max_iter, keep_trace);
   cudaStream_t st = stream_;
   const int np = ws.np;
   const int64_t ld = ws.ld, n = st_.n;

@@ -64,6 +64,7 @@ struct SolveState {
   bool on_device = false;
   int64_t n = 0;
   double lam = 0, ld_A = 0, trsa = 0, l1 = 0, F = 0;
+  double t_last = 1.0;   // G-ISTA: the last accepted step
   int k = 0;
   SolveOut out;
   std::chrono::steady_clock::time_point t_begin;
@@ -136,6 +137,7 @@ class Engine {
   void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);
+  int gista_step(double tol, int max_iter, bool keep_trace);
   double power_lambda_max(const double* M, cudaStream_t st);
   void sync_scalars();
 
