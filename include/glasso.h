@@ -87,6 +87,12 @@ typedef struct {
   int serve_slots;          /* requests the serving loop runs at once; default 8 */
   int products;             /* glasso_products: how the sandwich products of eq. b are formed */
   int method;               /* glasso_method; default GLASSO_METHOD_PISTA */
+  int standardize;          /* 1: every solve replaces S by its correlation matrix
+                               D^{-1/2} S D^{-1/2}, D = diag S (entry (i, j) computed as
+                               (S_ij d_i) d_j, d_i = 1 / sqrt(S_ii)), the preprocessing the
+                               paper applies to its gene-expression data (Sec. 6.2); the
+                               result is the estimate for the standardised problem.  S_ii
+                               must then be > 0 (else GLASSO_ERR_ARG).  Default 0. */
 } glasso_config;
 
 typedef struct {

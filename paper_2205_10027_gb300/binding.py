@@ -33,7 +33,7 @@ class glasso_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("precision", C.c_int),
                 ("max_iter", C.c_int), ("shrink", C.c_double), ("t_min", C.c_double),
                 ("hbm_budget_bytes", C.c_size_t), ("serve_slots", C.c_int), ("products", C.c_int),
-                ("method", C.c_int)]
+                ("method", C.c_int), ("standardize", C.c_int)]
 
 
 class glasso_result(C.Structure):
@@ -138,10 +138,11 @@ METHODS = {"pista": 0, "gista": 1}
 class Handle:
     """A library handle.  precision: 'fp64', 'tf32x3' or 'bf16x3'; products: how the sandwich
     products are formed, 'auto', 'dense' or 'sparse' (glasso_products); method: 'pista'
-    (Algorithm 1) or 'gista' (plain proximal gradient, glasso_method)."""
+    (Algorithm 1) or 'gista' (plain proximal gradient, glasso_method); standardize: solve on the
+    correlation matrix of S (glasso_config.standardize)."""
 
     def __init__(self, precision="fp64", device=0, stream=None, max_iter=500, shrink=0.5, t_min=1e-4,
-                 hbm_budget_bytes=0, serve_slots=8, products="auto", method="pista"):
+                 hbm_budget_bytes=0, serve_slots=8, products="auto", method="pista", standardize=False):
         cfg = glasso_config()
         glasso_config_default(C.byref(cfg))
         cfg.device = device
@@ -154,6 +155,7 @@ class Handle:
         cfg.serve_slots = serve_slots
         cfg.products = PRODUCTS[products]
         cfg.method = METHODS[method]
+        cfg.standardize = 1 if standardize else 0
         h = C.c_void_p()
         st = glasso_create(C.byref(cfg), C.byref(h))
         if st != OK:

@@ -71,6 +71,7 @@ glasso_status glasso_config_default(glasso_config* cfg) {
   cfg->serve_slots = 8;
   cfg->products = GLASSO_PRODUCTS_AUTO;
   cfg->method = GLASSO_METHOD_PISTA;
+  cfg->standardize = 0;
   return GLASSO_OK;
 }
 

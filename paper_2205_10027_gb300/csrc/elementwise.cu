@@ -219,6 +219,26 @@ __global__ void __launch_bounds__(RT) k_trial(const double* __restrict__ A,
   }
 }
 
+// ---- standardisation: d_i = 1 / sqrt(S_ii) (bad += 1 where S_ii <= 0), then for j <= i
+//      S_ij <- (S_ij d_i) d_j, mirrored to S_ji (the matrix stays exactly symmetric)
+__global__ void k_inv_sqrt_diag(const double* __restrict__ S, int64_t ld, int64_t n, double* d, int* bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = S[i * ld + i];
+  if (!(s > 0.0)) atomicAdd(bad, 1);
+  d[i] = 1.0 / sqrt(s);
+}
+__global__ void k_scale_rows_cols(double* __restrict__ S, int64_t ld, int64_t n, const double* __restrict__ d) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double di = d[i];
+    for (int64_t j = threadIdx.x; j <= i; j += blockDim.x) {
+      const double v = (S[i * ld + j] * di) * d[j];
+      S[i * ld + j] = v;
+      S[j * ld + i] = v;
+    }
+  }
+}
+
 // ---- G-ISTA candidate (Sec. 2.2 with H = I): At = ST(A - t g, t lam) with g = S - W, on
 //      32 x 32 tile pairs like k_trial (lower computed, mirrored; Lt = lower of At; identity
 //      padding), and partial sums of tr(S At), ||At||_1, nnz(At), <g, At - A>, ||At - A||_F^2
@@ -501,6 +521,13 @@ void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, co
   k_trial<<<g, RT, 0, st>>>(A, Y, code, ldc, S, ld, n, np, lam, t, At, Lt, parts);
   LAUNCH_CHECK();
   k_finalize<<<1, RT, 0, st>>>(parts, g, 5, out5);
+  LAUNCH_CHECK();
+}
+
+void standardize(double* S, int64_t ld, int64_t n, double* d, int* bad, cudaStream_t st) {
+  k_inv_sqrt_diag<<<(int)((n + 255) / 256), 256, 0, st>>>(S, ld, n, d, bad);
+  LAUNCH_CHECK();
+  k_scale_rows_cols<<<red_blocks(n), 256, 0, st>>>(S, ld, n, d);
   LAUNCH_CHECK();
 }
 

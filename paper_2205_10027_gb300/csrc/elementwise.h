@@ -23,6 +23,9 @@ void gradient(const double* S, const double* W, const double* A, int64_t ld, int
 void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, const double* S,
            int64_t ld, int64_t n, int np, double lam, double t, double* At, double* Lt,
            double* parts, double* out5, cudaStream_t st);
+// S (n x n block) <- D^{-1/2} S D^{-1/2}, D = diag S, as (S_ij d_i) d_j with d_i = 1/sqrt(S_ii)
+// (d: n doubles of scratch); *bad += the number of S_ii <= 0 (bad must be 0 on entry).
+void standardize(double* S, int64_t ld, int64_t n, double* d, int* bad, cudaStream_t st);
 // G-ISTA candidate (proximal gradient with H = I): At (full) = ST(A - t (S - W), t lam) on
 // the n x n block (identity padding), Lt (lower) = At, and out5 = {tr(S At), ||At||_1,
 // nnz(At), <S - W, At - A>, ||At - A||_F^2}.

@@ -537,6 +537,14 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   const size_t mat = sizeof(double) * ld * np;
   Scalars& h = *ws.hs;
   load_matrix(Sin, s_f32, s_on_device, n, ws.S, true);
+  if (cfg_.standardize) {
+    int bad = 0;
+    CUDA_CHECK(cudaMemsetAsync(ws.bad, 0, sizeof(int), st));
+    standardize(ws.S, ld, n, ws.vec, ws.bad, st);
+    CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (bad) throw Error(GLASSO_ERR_ARG, "standardize needs every S_ii > 0");
+  }
   CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ld * np, st));
   CUDA_CHECK(cudaMemsetAsync(ws.X, 0, mat, st));
   if (theta0) {

@@ -214,3 +214,23 @@ def test_profile_mixed_classes(glasso):
         prof = h.profile_stop()
     for cls in ("residual", "aux", "sandwich", "inverse"):
         assert prof[cls]["launches"] > 0 and prof[cls]["ms"] > 0 and prof[cls]["work"] > 0
+
+
+def test_standardized_solve_follows_the_oracle_on_the_correlation_matrix(glasso):
+    """glasso_config.standardize: the solve runs on D^{-1/2} S D^{-1/2} (entry (S_ij d_i) d_j
+    on the lower triangle, mirrored), so it takes the oracle's path on that matrix."""
+    p = inputs.chain_n100()
+    S = p.S * np.linspace(0.5, 3.0, p.S.shape[0])[:, None] * np.linspace(0.5, 3.0, p.S.shape[0])[None, :]
+    S = 0.5 * (S + S.T)
+    d = 1.0 / np.sqrt(np.diag(S))
+    C = (S * d[:, None]) * d[None, :]
+    C = np.tril(C) + np.tril(C, -1).T
+    with glasso.Handle(precision="fp64", standardize=True) as h:
+        theta, res = h.solve(S, p.lam, 1e-8)
+        with pytest.raises(glasso.GlassoError) as e:
+            Z = S.copy()
+            Z[3, 3] = 0.0
+            h.solve(Z, p.lam, 1e-8)
+        assert e.value.status == 1
+    ref = pista.pista(C, p.lam, tol=1e-8)
+    _same_path(res, theta, ref)
