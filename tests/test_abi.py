@@ -67,3 +67,49 @@ def test_create_without_a_gpu_is_refused_cleanly(glasso):
     h = C.c_void_p()
     assert glasso.glasso_create(C.byref(cfg), C.byref(h)) == 12  # GLASSO_ERR_UNSUPPORTED
     assert not h.value
+
+
+def _header_text():
+    return re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+
+
+def _enum_values(prefix):
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]+)\s*=\s*(\d+)", _header_text())}
+
+
+def _struct_fields(name):
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", _header_text()).group(1)
+    fields = []
+    for decl in body.split(";"):
+        for part in decl.split(","):  # "double a, b, c" declares three fields
+            part = part.split("[")[0].strip()
+            if part:
+                fields.append(re.findall(r"[A-Za-z_][A-Za-z_0-9]*", part)[-1])
+    return fields
+
+
+def test_binding_constants_match_the_header(glasso):
+    st = _enum_values("GLASSO_")
+    for code, name in glasso.STATUS.items():
+        assert st[name] == code, name
+    for key, value in glasso.PRECISION.items():
+        assert value == {"fp64": st["GLASSO_FP64"], "tf32x3": st["GLASSO_MIXED_TF32X3"],
+                         "bf16x3": st["GLASSO_MIXED_BF16X3"]}[key]
+    for key, value in glasso.PRODUCTS.items():
+        assert st["GLASSO_PRODUCTS_" + key.upper()] == value
+    for key, value in glasso.METHODS.items():
+        assert st["GLASSO_METHOD_" + key.upper()] == value
+    prof = _enum_values("GLASSO_PROF_")
+    assert prof.pop("GLASSO_PROF_CLASSES") == len(glasso.PROF_CLASSES)
+    for name, idx in prof.items():
+        assert glasso.PROF_CLASSES[idx] == name[len("GLASSO_PROF_"):].lower()
+
+
+def test_binding_structures_follow_the_header_field_order(glasso):
+    structs = [n for n in dir(glasso) if n.startswith("glasso_") and isinstance(getattr(glasso, n), type)
+               and issubclass(getattr(glasso, n), C.Structure)]
+    assert {"glasso_config", "glasso_result", "glasso_profile"} <= set(structs)
+    for cname in structs:
+        py = getattr(glasso, cname)
+        # (a trailing underscore stands for a Python keyword: lambda_)
+        assert _struct_fields(cname) == [f.rstrip("_") for f, _ in py._fields_], cname
