@@ -107,6 +107,14 @@ typedef struct {
   double seconds;           /* wall time of the solve inside the library */
   double t_submit, t_start, t_done;  /* serving timestamps (s, monotonic clock), else 0 */
   int64_t kernel_launches;  /* CUDA kernels this solve (or step) launched */
+  /* The last line search (glasso_step: this call's, all 0 when the call formed no
+   * direction; glasso_solve: the solve's last one, accepted or refused): */
+  double step_t;            /* step size of the last trial (Sec. 4.3.2 halving or the Sec. 6
+                               fallback t = (0.9 / cond Theta)^2) */
+  double step_dF;           /* F(Theta_t) - F(Theta) the accept test saw (eq. t_cond_min) */
+  int32_t step_tier;        /* 1: dF from the two Cholesky log-dets; 2: the log-det
+                               difference re-evaluated from Theta^{-1} near the decision */
+  int32_t step_fallback;    /* 1 if halving went below t_min and the fallback step was tried */
 } glasso_result;
 
 /* ---- handle ------------------------------------------------------------------------------ */
@@ -289,9 +297,11 @@ glasso_status glasso_op_trial(glasso_handle* h, const double* A, const double* Y
  *   sums      device output of 4 doubles: ||Z||_1, ||A||_1, ||Z||_F^2, nnz(A).
  *   stream    cudaStream_t to run on (NULL: the legacy default stream).
  * Runs on the device that is current for the calling thread and returns once the work is
- * queued on `stream` (the outputs are ready when the stream reaches it).  The first call on
- * a device looks up the device address of the scratch array (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call on a device
+ * queued on `stream` (the outputs are ready when the stream reaches it).  The first call in
+ * a CUDA context looks up the device address of the scratch array there (cudaGetSymbolAddress)
+ * and caches it under the context's unique id, so a new context -- after cudaDeviceReset, or
+ * a driver-API context other than the device's primary one -- gets its own address; make the
+ * first call in each context before any stream capture.  Every call on a device
  * shares the one scratch array and overwrites its first n rows, so nothing in it has to
  * start at zero; calls whose work overlaps on the GPU (different streams, or graphs replayed
  * concurrently) race on it and must be serialised by the caller.

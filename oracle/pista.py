@@ -185,6 +185,13 @@ def cond2(A):
     return float(ev[-1] / ev[0])
 
 
+def fallback_step(A):
+    """t_f = (0.9 / cond_2(A))^2: the step of Sec. 6 once halving has gone below t_min
+    (reading R5).  Lemma 4.1 bounds an acceptable step by (beta / gamma)^2 with beta, gamma
+    bounds of the eigenvalues; Sec. 6 takes the current iterate's own, with the factor 0.9."""
+    return (FALLBACK_FACTOR / cond2(A)) ** 2
+
+
 # ----------------------------------------------------------------------------------------
 # step functions (what one GPU kernel computes, for kernel-level parity)
 # ----------------------------------------------------------------------------------------
@@ -209,8 +216,14 @@ def step_sandwich(A, X):
 # ----------------------------------------------------------------------------------------
 # Algorithm 1
 # ----------------------------------------------------------------------------------------
-def pista(S, lam, tol, A0=None, max_iter=500, shrink=0.5, t_min=T_MIN, trace=False):
+def pista(S, lam, tol, A0=None, max_iter=500, shrink=0.5, t_min=T_MIN, trace=False,
+          fallback=None, trace_iterates=False):
     """pISTA(S, lam, A0) of Algorithm 1 with the readings R1-R12.
+
+    fallback: optional callable (k, A) -> t replacing fallback_step(A) at outer iteration k
+    (a test replays with it the step sizes another implementation took).
+    trace_iterates: each trace record also keeps the iterate ("theta") and the last trial
+    point ("trial") of its iteration.
 
     Returns a dict: theta, F, r (relative l1 KKT residual), z_fro, nnz, iterations,
     trials (line-search trials in total), status in {"converged", "max_iter", "stall"},
@@ -255,7 +268,7 @@ def pista(S, lam, tol, A0=None, max_iter=500, shrink=0.5, t_min=T_MIN, trace=Fal
                 break
             t *= shrink
         if not accepted:
-            t = (FALLBACK_FACTOR / cond2(A)) ** 2
+            t = fallback_step(A) if fallback is None else float(fallback(k, A))
             At = trial(A, B, C, M, t)
             dF, tier = objective_difference(S, A, L, At, lam, delta)
             trials += 1
@@ -265,6 +278,8 @@ def pista(S, lam, tol, A0=None, max_iter=500, shrink=0.5, t_min=T_MIN, trace=Fal
             hist.append(dict(k=k, F=F, r=r, z_fro=zf, nnz=int(np.count_nonzero(A)), t=t,
                              trials=trials, accepted=accepted, dF=dF, tier=tier,
                              delta=delta))
+            if trace_iterates:
+                hist[-1].update(theta=A, trial=At)
         if not accepted:
             status = "stall"
             break

@@ -41,7 +41,8 @@ class glasso_result(C.Structure):
                 ("nnz", C.c_int32), ("rel_kkt_l1", C.c_double), ("min_subgrad_fro", C.c_double),
                 ("objective", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
                 ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("step_t", C.c_double), ("step_dF", C.c_double),
+                ("step_tier", C.c_int32), ("step_fallback", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -47,6 +47,10 @@ void fill_result(glasso_result* res, const glasso::SolveOut& o) {
   res->logdet = o.logdet;
   res->seconds = o.seconds;
   res->kernel_launches = o.launches;
+  res->step_t = o.step_t;
+  res->step_dF = o.step_dF;
+  res->step_tier = o.step_tier;
+  res->step_fallback = o.step_fallback;
 }
 
 bool valid_problem(int64_t n, double lambda, double tol) {
@@ -185,6 +189,12 @@ glasso_status glasso_step(glasso_handle* h, double tol, glasso_result* res) {
       o.F = s.F;
       o.logdet = s.ld_A;
       o.launches = glasso::thread_launches() - l0;
+      if (o.trials > 0) {  // this call formed a direction and ran a line search
+        o.step_t = s.out.step_t;
+        o.step_dF = s.out.step_dF;
+        o.step_tier = s.out.step_tier;
+        o.step_fallback = s.out.step_fallback;
+      }
       fill_result(res, o);
     }
     return st < 0 ? GLASSO_PENDING : (glasso_status)st;

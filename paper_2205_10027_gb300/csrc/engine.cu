@@ -632,6 +632,10 @@ int Engine::gista_step(double tol, int max_iter, bool keep_trace) {
     }
   }
   out.trials += trials;
+  out.step_t = t;
+  out.step_dF = 0.0;
+  out.step_tier = 1;
+  out.step_fallback = 0;
   if (keep_trace) out.trace.push_back(IterRecord{st_.k, trials, 1, st_.F, out.r, out.z_fro, out.nnz, t, 0.0});
   if (!accepted) return GLASSO_LINESEARCH_STALL;
   std::swap(ws.A, ws.At);
@@ -713,7 +717,9 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
     if (dF < 0.0) { accepted = true; break; }
     t *= shrink;
   }
+  bool fallback = false;
   if (!accepted) {
+    fallback = true;
     const double lmax_a = power_lambda_max(ws.A, st);
     const double lmax_w = power_lambda_max(ws.W, st);
     t = std::pow(kFallbackFactor / (lmax_a * lmax_w), 2.0);
@@ -721,6 +727,10 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
     accepted = dF < 0.0;
   }
   out.trials += trials;
+  out.step_t = t;
+  out.step_dF = dF;
+  out.step_tier = tier;
+  out.step_fallback = fallback ? 1 : 0;
   if (keep_trace)
     out.trace.push_back(IterRecord{st_.k, trials, tier, st_.F, out.r, out.z_fro, out.nnz, t, dF});
   if (!accepted) return GLASSO_LINESEARCH_STALL;

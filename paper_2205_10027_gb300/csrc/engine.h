@@ -55,6 +55,9 @@ struct SolveOut {
   int iterations = 0, trials = 0;
   double r = 0, z_fro = 0, F = 0, logdet = 0, nnz = 0, seconds = 0;
   int64_t launches = 0;
+  // the last line search: its final trial step, dF, tier and whether the fallback ran
+  double step_t = 0, step_dF = 0;
+  int step_tier = 0, step_fallback = 0;
   std::vector<IterRecord> trace;
 };
 

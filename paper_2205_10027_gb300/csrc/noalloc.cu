@@ -8,6 +8,7 @@
 // row -- in the file-scope device array below, which the library's module owns for the
 // lifetime of the process on every GPU that loads it.
 #include <mutex>
+#include <unordered_map>
 #include "../../include/glasso.h"
 #include "common.cuh"
 
@@ -64,9 +65,73 @@ __global__ void k_sum_rows(const double* __restrict__ part, int64_t n, double* _
   }
 }
 
-constexpr int kMaxDevices = 64;
+// The device address of the scratch array belongs to the module instance of one CUDA
+// context: after cudaDeviceReset, or under a driver-API context other than the device's
+// primary one, the module is loaded again at another address.  The cached address is
+// therefore keyed on the unique id of the calling thread's current context (cuCtxGetId),
+// looked up through the runtime's driver entry points so that the library does not link
+// libcuda directly.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+struct DriverFns {
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+};
+
+const DriverFns& driver_fns() {
+  static DriverFns fns;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fns.get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    else
+      cudaGetLastError();
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fns.get_id = reinterpret_cast<CtxGetIdFn>(f);
+    else
+      cudaGetLastError();
+  });
+  return fns;
+}
+
 std::mutex g_setup_mu;
-double* g_scratch_addr[kMaxDevices] = {};
+std::unordered_map<unsigned long long, double*> g_scratch_by_ctx;  // context id -> address
+
+// Address of the scratch array in the calling thread's current context, looked up (once per
+// context) with cudaGetSymbolAddress; nullptr on failure.
+double* scratch_address() {
+  const DriverFns& fns = driver_fns();
+  if (!fns.get_current || !fns.get_id) return nullptr;
+  // a thread with no current context gets its device's primary context (cudaSetDevice
+  // initialises and binds it)
+  void* ctx = nullptr;
+  if (fns.get_current(&ctx) != 0 || !ctx) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (fns.get_current(&ctx) != 0 || !ctx) return nullptr;
+  }
+  unsigned long long id = 0;
+  if (fns.get_id(ctx, &id) != 0) return nullptr;
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  auto it = g_scratch_by_ctx.find(id);
+  if (it != g_scratch_by_ctx.end()) return it->second;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_scratch_by_ctx.emplace(id, static_cast<double*>(p));
+  return static_cast<double*>(p);
+}
 
 }  // namespace
 }  // namespace glasso
@@ -77,25 +142,9 @@ extern "C" glasso_status glasso_gradient_noalloc(const double* S, const double* 
   using namespace glasso;
   if (!S || !A || !W || !X || !code || !sums || n < 1 || !(lambda > 0.0)) return GLASSO_ERR_ARG;
   if (n > GLASSO_NOALLOC_MAX_N) return GLASSO_ERR_BUDGET;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return GLASSO_ERR_CUDA;
-  }
-  double* scratch = nullptr;
-  {
-    // set-up, once per device, with that device current: the device address of the array
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return GLASSO_ERR_CUDA;
-      }
-      g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_scratch_addr[dev];
-  }
+  // set-up, once per context, with the caller's device current: the array's device address
+  double* scratch = scratch_address();
+  if (!scratch) return GLASSO_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_gradient_rows<<<(unsigned)n, 256, 0, st>>>(S, A, W, n, lambda, X, code, scratch);
   if (cudaGetLastError() != cudaSuccess) return GLASSO_ERR_CUDA;

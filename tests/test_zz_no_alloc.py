@@ -28,10 +28,24 @@ def _problem(n, seed):
     return S, A, pista.inverse(A)
 
 
+def _device_problem(n, seed):
+    """A large (S, A, W) triple generated on the device; the gradient pass needs no relation
+    between A and W, only their shapes and values."""
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    S = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g) * 0.1
+    S = 0.5 * (S + S.T)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    A = A * (torch.rand((n, n), device="cuda", generator=g) < 0.01)
+    A = 0.5 * (A + A.T) + torch.eye(n, dtype=torch.float64, device="cuda")
+    W = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g) * 0.1
+    return [S.contiguous(), A.contiguous(), (0.5 * (W + W.T)).contiguous()]
+
+
 def test_noalloc_matches_op_gradient_on_two_calls(glasso):
     lam = 0.05
     cases = [_problem(257, 1), _problem(100, 2)]   # second call smaller: stale scratch rows
     dev = [[torch.from_numpy(m).cuda() for m in c] for c in cases]
+    dev.append(_device_problem(glasso.NOALLOC_MAX_N, 3))   # third call: the largest n allowed
     outs = []
     for (S, A, W) in dev:
         n = S.shape[0]
@@ -40,7 +54,7 @@ def test_noalloc_matches_op_gradient_on_two_calls(glasso):
                      torch.empty(4, dtype=torch.float64, device="cuda")))
     stream = torch.cuda.current_stream().cuda_stream
     torch.cuda.synchronize()
-    free = []
+    free, held = [], []
     for (S, A, W), (X, code, sums) in zip(dev, outs):
         n = S.shape[0]
         st = glasso.glasso_gradient_noalloc(S.data_ptr(), A.data_ptr(), W.data_ptr(), n, lam,
@@ -48,7 +62,11 @@ def test_noalloc_matches_op_gradient_on_two_calls(glasso):
         assert st == 0
         torch.cuda.synchronize()
         free.append(torch.cuda.mem_get_info()[0])
-    assert free[1] == free[0]   # the second call allocated nothing
+        held.append(torch.cuda.memory_allocated())
+    # nothing allocated through torch by any call, and no device memory taken by the calls
+    # after the first (the first may load the library's module, which holds the scratch array)
+    assert held[0] == held[1] == held[2]
+    assert free[0] == free[1] == free[2]
     with glasso.Handle(precision="fp64") as h:
         for (S, A, W), (X, code, sums) in zip(dev, outs):
             Xr, coder, sumsr = h.op_gradient(S, A, W, lam)
