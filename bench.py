@@ -135,6 +135,76 @@ def oracle_rate(sample_side: int, full_n: int, iters: int):
     return rate, dt, res["iterations"], ns
 
 
+def oracle_full_iteration(side: int, m: int):
+    """One oracle iteration of the workload itself (n = side^2), from its start point:
+    (iterations/s, seconds, iterations, line-search trials)."""
+    from oracle import pista
+    p = workload(side, m)
+    t0 = time.perf_counter()
+    res = pista.pista(p.S, p.lam, tol=0.0, max_iter=1, trace=True)
+    dt = time.perf_counter() - t0
+    return res["iterations"] / dt, dt, res["iterations"], res["trace"][0]["trials"]
+
+
+# Kernel classes of the step (glasso_profile) and what bounds each: FLOP classes on the tensor
+# pipe (split-precision products, FLOPs counted once, the narrow type's peak / 3) or on the FP64
+# pipe; byte classes on HBM.
+CLASS_BOUND = {"factor": "tensor", "inverse": "tensor", "refine": "tensor", "sandwich": "tensor",
+               "trailing": "tensor", "panel": "tensor", "spmm": "fp64",
+               "gradient": "hbm", "trial": "hbm", "residual": "hbm", "logdet2": "hbm", "aux": "hbm"}
+CLASS_UNIT = {"factor": "whole Cholesky-with-inverse factorisations (one CUDA graph each: k_gemm_tc, k_split, "
+                        "k_gemm_f32, k_leaf64)",
+              "inverse": "W = X^T X (k_gemm_tc)", "refine": "refinement product W R (k_gemm_tc)",
+              "sandwich": "dense sandwich products (k_gemm_tc)", "spmm": "sparse sandwich products (k_spmm)",
+              "gradient": "gradient pass (k_gradient)", "trial": "trial-point pass (k_trial)",
+              "residual": "FP64 residual I - Theta W (k_spmm residual epilogue)",
+              "logdet2": "second-order log-det difference (CSR of dTheta, k_spmm, k_trace_pairs)",
+              "aux": "symmetrising copies (k_mirror_lower, k_add_lower_mirror)"}
+
+
+def roofline_by_class(prof: dict, step_ms_total: float, args, n: int, fp64_peak_live: float) -> dict:
+    """Per kernel class of the timed steps: share of the device time, achieved rate on its
+    algorithmic work, the peak that bounds it and the fraction; the roofline object names the
+    class with the largest share.  Peaks: MEASURED_PEAKS.json (HBM copy, cuBLAS BF16 sustained x
+    the nominal TF32/BF16 ratio / 3 split products); the FP64 pipe from the recipe's unit
+    counts: 2 DFMA lanes / clock / SM (measured by glasso_probe_fp64_peak) x 152 SMs x the max
+    SM clock x 2 FLOPs."""
+    peaks, kind = _peaks()
+    fp64_peak = 2.0 * 2.0 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if args.precision == "fp64":
+        tensor_peak, tensor_src = fp64_peak, "FP64 pipe (2 DFMA/clk/SM x 152 SMs x max clock)"
+    else:
+        ratio = (1100.0 / 2250.0) if args.precision == "tf32x3" else 1.0
+        tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0) * ratio / 3.0
+        tensor_src = f"{kind}: bf16 sustained x nominal dtype ratio / 3 split products"
+    classes = {}
+    for c, v in prof.items():
+        if not v["ms"] or c not in CLASS_BOUND:
+            continue
+        bound = CLASS_BOUND[c]
+        if bound == "hbm":
+            unit, achieved, peak, src = "GB/s", v["work"] / (v["ms"] / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0), kind
+        elif bound == "fp64":
+            unit, achieved, peak, src = "TFLOP/s", v["work"] / (v["ms"] / 1e3) / 1e12, fp64_peak, "FP64 pipe"
+        else:
+            unit, achieved, peak, src = "TFLOP/s", v["work"] / (v["ms"] / 1e3) / 1e12, tensor_peak, tensor_src
+            if args.precision == "fp64":
+                bound = "alu"
+        classes[c] = {"unit_of_work": CLASS_UNIT.get(c, c), "ms": v["ms"], "launches": v["launches"],
+                      "share": v["ms"] / step_ms_total if step_ms_total else None, "bound": bound,
+                      "achieved": achieved, "unit": unit, "peak": peak, "peak_source": src,
+                      "frac": achieved / peak if peak else None}
+    dom = max(classes, key=lambda c: classes[c]["ms"])
+    d = classes[dom]
+    traffic = None
+    if dom in ("inverse", "refine") and args.precision in TC_TRAFFIC_PER_LAUNCH and args.side == 100:
+        traffic = TC_TRAFFIC_PER_LAUNCH[args.precision]
+    return {"bound": d["bound"], "kernel": dom, "unit_of_work": d["unit_of_work"], "achieved": d["achieved"],
+            "peak": d["peak"], "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+            "share_of_step": d["share"], "launches": d["launches"], "peak_source": d["peak_source"],
+            "fp64_probe_tflops": fp64_peak_live, "classes": classes}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -184,7 +254,7 @@ def run_ours(args):
     n = p.S.shape[0]
     S_dev = torch.from_numpy(np.ascontiguousarray(p.S)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream,
                        products=args.products, method=args.method)
 
     def barrier():
@@ -219,7 +289,7 @@ def run_ours(args):
     # ---- end to end through the public API, host buffers ------------------------------------
     S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
     out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    he = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream,
+    he = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream,
                         max_iter=args.steps, products=args.products, method=args.method)
     he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())  # warm the workspace
     barrier()
@@ -233,7 +303,7 @@ def run_ours(args):
     # ---- time to tolerance (device-resident) ---------------------------------------------------
     ttt = None
     if args.time_to_tol:
-        ht = binding.Handle(precision=args.precision, device=local, stream=stream.cuda_stream, max_iter=2000,
+        ht = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream, max_iter=2000,
                             products=args.products, method=args.method)
         barrier()
         t0 = time.perf_counter()
@@ -270,44 +340,21 @@ def run_ours(args):
     h.close()
 
     if rank == 0:
-        peaks, peak_kind = _peaks()
-        # dominant kernel: the dense-product kernel (all GEMM classes are launches of it)
-        gemm_cls = [c for c in ("sandwich", "trailing", "panel", "inverse", "refine") if c in prof]
-        # (the "factor" class spans whole factorisations and overlaps the GEMM classes)
-        g_ms = sum(prof[c]["ms"] for c in gemm_cls)
-        g_work = sum(prof[c]["work"] for c in gemm_cls)
-        g_launch = sum(prof[c]["launches"] for c in gemm_cls)
-        achieved = g_work / (g_ms / 1000.0) / 1e12 if g_ms else 0.0
-        if args.precision == "fp64":
-            # FP64 runs on the CUDA cores' FP64 pipe: peak measured live by an FMA-chain kernel
-            peak = binding.probe_fp64_peak(local)
-            peak_kind = "measured live (FP64 FMA-chain kernel in libglasso)"
-            bound, kernel = "alu", "k_gemm_f64"
-        else:
-            ratio = (1100.0 / 2250.0) if args.precision == "tf32x3" else 1.0
-            peak = peaks.get("bf16_tflops_sustained", 1700.0) * ratio / 3.0
-            bound, kernel = "tensor", "k_gemm_tc"
-        rl = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-              "frac": achieved / peak if peak else None,
-              "traffic": TC_TRAFFIC_PER_LAUNCH.get(args.precision) if args.side == 100 and args.m == 2000 else None,
-              "peak_source": peak_kind if args.precision == "fp64" else f"{peak_kind} bf16 sustained x nominal dtype ratio / 3 split products",
-              "launches": g_launch, "share_of_step": g_ms / ms if ms else None}
-        if "factor" in prof and prof["factor"]["ms"]:
-            # the factorisations replay as CUDA graphs: timed as whole graphs (2 n^3 / 3 FLOPs)
-            rl["factor_graph"] = {"ms": prof["factor"]["ms"], "launches": prof["factor"]["launches"],
-                                  "tflops": prof["factor"]["work"] / (prof["factor"]["ms"] / 1e3) / 1e12}
-        hbm = {}
-        for c in ("gradient", "trial"):
-            if c in prof and prof[c]["ms"]:
-                gbs = prof[c]["work"] / (prof[c]["ms"] / 1000.0) / 1e9
-                hbm[c] = {"achieved_gbs": gbs, "frac": gbs / peaks.get("hbm_gbs", 6800.0),
-                          "launches": prof[c]["launches"], "ms": prof[c]["ms"]}
+        rl = roofline_by_class(prof, ms, args, n, binding.probe_fp64_peak(local))
+        hbm = {c: v for c, v in rl["classes"].items() if v["bound"] == "hbm"}
         cpu = None
         if not args.no_cpu_baseline:
-            rate, dt, its, ns = oracle_rate(args.sample_side, n, 2)
+            # measured on the workload itself: one full oracle iteration at n (no scaling); the
+            # bounded smaller-lattice sample of the reference arm is reported beside it
+            rate, dt, its, trials = oracle_full_iteration(args.side, args.m)
             cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"{its} oracle iterations on a {args.sample_side}x{args.sample_side} lattice "
-                             f"(n={ns}, m=n/5) in {dt:.1f}s, scaled to n={n} by (n_sample/n)^3"}
+                   "sample": f"measured at n={n}: {its} full oracle iteration ({trials} line-search trials) "
+                             f"from the start point of the {args.side}x{args.side} lattice workload in {dt:.1f}s"}
+            srate, sdt, sits, ns = oracle_rate(args.sample_side, n, 1)
+            cpu["scaled_sample"] = {
+                "value": srate, "unit": UNIT,
+                "sample": f"{sits} oracle iteration on a {args.sample_side}x{args.sample_side} lattice (n={ns}, m=n/5) "
+                          f"in {sdt:.1f}s, scaled to n={n} by (n_sample/n)^3 (the reference arm's sample)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -347,7 +394,7 @@ def run_op(args):
     X = 0.5 * (X + X.T)
     Ad, Xd = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
     Sd = torch.from_numpy(p.S + np.eye(n)).cuda()
-    h = binding.Handle(precision=args.precision, products=args.products)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, products=args.products)
     fn = (lambda: h.op_sandwich(Ad, Xd)) if args.op == "sandwich" else (lambda: h.op_cholesky(Sd))
     for _ in range(args.warmup):
         fn()
@@ -384,7 +431,7 @@ def run_paper_table(args):
     tab = PAPER_TABLES[args.paper_table]
     n = tab["n"]
     seeds = args.paper_seeds
-    h = binding.Handle(precision=args.precision, max_iter=1000)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, max_iter=1000)
     rows = []
     for kind, alpha, paper_s, paper_it in tab["rows"]:
         times, its, nnz, mcc = [], [], [], []
@@ -418,7 +465,7 @@ def run_batch(args):
     probs = inputs.batch_path_problems(count=args.batch_count, seed=3)
     for p in probs:
         p["tol"] = args.batch_tol
-    h = binding.Handle(precision=args.precision, serve_slots=args.slots, max_iter=args.batch_max_iter)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, serve_slots=args.slots, max_iter=args.batch_max_iter)
     warm = inputs.batch_path_problems(count=min(4, len(probs)), seed=97)
     for p in warm:
         p["tol"] = args.batch_tol
@@ -452,7 +499,7 @@ def run_served(args):
 
     for d in sorted(set(ids.tolist())):
         S_of(int(d))
-    h = binding.Handle(precision=args.precision, serve_slots=args.slots,
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, serve_slots=args.slots,
                        hbm_budget_bytes=int(args.budget_gb * 1e9), max_iter=args.batch_max_iter)
     t_start = time.perf_counter()
     tickets = []
@@ -504,6 +551,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="bf16x3")
     ap.add_argument("--method", choices=["pista", "gista"], default="pista",
                     help="outer method (glasso_method): Algorithm 1, or plain proximal gradient")
+    ap.add_argument("--fp32-panels", action="store_true",
+                    help="split-precision forms: factor the Cholesky panels in FP32 (default FP64)")
     ap.add_argument("--products", choices=["auto", "dense", "sparse"], default="auto",
                     help="how the sandwich products are formed (glasso_products)")
     ap.add_argument("--side", type=int, default=100)

@@ -50,9 +50,11 @@ typedef enum {
 typedef enum {
   GLASSO_FP64 = 0,          /* every step in FP64 */
   GLASSO_MIXED_TF32X3 = 1,  /* dense products wider than 256 on the tensor cores with
-                               3-term TF32 splits, smaller ones and the 128 x 128 Cholesky
-                               leaves in FP32 arithmetic; FP64 storage, W refined to FP64
-                               accuracy, FP64 line-search and stop decisions */
+                               3-term TF32 splits, smaller ones in FP32 arithmetic, all added
+                               to FP64 storage in FP64; Cholesky panels in FP64 (see
+                               glasso_config.fp32_panels); W refined to FP64 accuracy; every
+                               accepted trial certified PD in FP64; FP64 line-search and stop
+                               decisions */
   GLASSO_MIXED_BF16X3 = 2   /* as GLASSO_MIXED_TF32X3 with 3-term BF16 splits */
 } glasso_precision;
 
@@ -93,6 +95,13 @@ typedef struct {
                                paper applies to its gene-expression data (Sec. 6.2); the
                                result is the estimate for the standardised problem.  S_ii
                                must then be > 0 (else GLASSO_ERR_ARG).  Default 0. */
+  int fp32_panels;          /* split-precision modes only.  0 (default): the Cholesky panels
+                               (64 x 64 diagonal blocks) are factored in FP64, so the pivots,
+                               the PD test and the log det are FP64 arithmetic on the FP64
+                               Schur complement; the inverse of each block's factor, which
+                               only feeds split-precision products, is formed in FP32.
+                               1: 128 x 128 panels factored and inverted in FP32 (faster,
+                               FP32-grade pivots). */
 } glasso_config;
 
 typedef struct {
@@ -206,6 +215,11 @@ glasso_status glasso_profile_stop(glasso_handle* h, glasso_profile* out);
 /* Peak FP64 FMA throughput of a device in TFLOP/s, measured by a register-resident FMA
  * kernel (the roofline denominator of the FP64 form; it allocates a small buffer). */
 glasso_status glasso_probe_fp64_peak(int device, double* tflops);
+
+/* Device memory one solve of size n holds on a handle (its workspace: the n x n iterates,
+ * factors, products and scratch, padded to a multiple of 128), the figure the HBM budget of
+ * glasso_config and the serving loop's admission count per slot.  GLASSO_ERR_ARG for n < 1. */
+glasso_status glasso_workspace_bytes(int64_t n, size_t* bytes);
 
 /* ---- batched regularisation paths -------------------------------------------------------- */
 

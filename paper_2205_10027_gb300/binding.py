@@ -33,7 +33,7 @@ class glasso_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("precision", C.c_int),
                 ("max_iter", C.c_int), ("shrink", C.c_double), ("t_min", C.c_double),
                 ("hbm_budget_bytes", C.c_size_t), ("serve_slots", C.c_int), ("products", C.c_int),
-                ("method", C.c_int), ("standardize", C.c_int)]
+                ("method", C.c_int), ("standardize", C.c_int), ("fp32_panels", C.c_int)]
 
 
 class glasso_result(C.Structure):
@@ -89,6 +89,7 @@ _sig = {
     "glasso_profile_stop": (C.c_int, [_h, C.POINTER(glasso_profile)]),
     "glasso_probe_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "glasso_gradient_noalloc": (C.c_int, [_dp, _dp, _dp, C.c_int64, C.c_double, _dp, _dp, _dp, _dp]),
+    "glasso_workspace_bytes": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
     "glasso_solve_batch": (C.c_int, [_h, C.POINTER(glasso_problem), C.c_int32, C.POINTER(glasso_result)]),
     "glasso_submit": (C.c_int, [_h, C.POINTER(glasso_request), C.POINTER(C.c_uint64)]),
     "glasso_poll": (C.c_int, [_h, C.c_uint64, C.POINTER(glasso_result), _dp]),
@@ -132,6 +133,15 @@ def probe_fp64_peak(device=0):
     return v.value
 
 
+def workspace_bytes(n):
+    """Device memory one solve of size n holds (glasso_workspace_bytes)."""
+    v = C.c_size_t()
+    st = glasso_workspace_bytes(n, C.byref(v))
+    if st != OK:
+        raise GlassoError(st, "glasso_workspace_bytes failed")
+    return v.value
+
+
 PRODUCTS = {"auto": 0, "dense": 1, "sparse": 2}
 METHODS = {"pista": 0, "gista": 1}
 
@@ -140,10 +150,12 @@ class Handle:
     """A library handle.  precision: 'fp64', 'tf32x3' or 'bf16x3'; products: how the sandwich
     products are formed, 'auto', 'dense' or 'sparse' (glasso_products); method: 'pista'
     (Algorithm 1) or 'gista' (plain proximal gradient, glasso_method); standardize: solve on the
-    correlation matrix of S (glasso_config.standardize)."""
+    correlation matrix of S (glasso_config.standardize); fp32_panels: factor the Cholesky panels
+    of the split-precision forms in FP32 instead of FP64 (glasso_config.fp32_panels)."""
 
     def __init__(self, precision="fp64", device=0, stream=None, max_iter=500, shrink=0.5, t_min=1e-4,
-                 hbm_budget_bytes=0, serve_slots=8, products="auto", method="pista", standardize=False):
+                 hbm_budget_bytes=0, serve_slots=8, products="auto", method="pista", standardize=False,
+                 fp32_panels=False):
         cfg = glasso_config()
         glasso_config_default(C.byref(cfg))
         cfg.device = device
@@ -157,6 +169,7 @@ class Handle:
         cfg.products = PRODUCTS[products]
         cfg.method = METHODS[method]
         cfg.standardize = 1 if standardize else 0
+        cfg.fp32_panels = 1 if fp32_panels else 0
         h = C.c_void_p()
         st = glasso_create(C.byref(cfg), C.byref(h))
         if st != OK:

@@ -76,6 +76,7 @@ glasso_status glasso_config_default(glasso_config* cfg) {
   cfg->products = GLASSO_PRODUCTS_AUTO;
   cfg->method = GLASSO_METHOD_PISTA;
   cfg->standardize = 0;
+  cfg->fp32_panels = 0;
   return GLASSO_OK;
 }
 
@@ -236,6 +237,12 @@ glasso_status glasso_probe_fp64_peak(int device, double* tflops) {
     *tflops = glasso::probe_fp64_tflops(device);
     return GLASSO_OK;
   });
+}
+
+glasso_status glasso_workspace_bytes(int64_t n, size_t* bytes) {
+  if (!bytes || n < 1 || n > ((int64_t)1 << 20)) return GLASSO_ERR_ARG;
+  *bytes = glasso::Workspace::bytes_for((int)glasso::round_up(n, glasso::kPad));
+  return GLASSO_OK;
 }
 
 glasso_status glasso_solve_batch(glasso_handle* h, const glasso_problem* probs, int32_t count,

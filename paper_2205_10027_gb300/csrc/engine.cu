@@ -47,6 +47,66 @@ __global__ void k_fill(double* x, int64_t n, double v) {
   if (j < n) x[j] = v;
 }
 
+// ---- FP64 positive-definiteness certificate of a trial point (split-precision forms) ----
+// M = X A X^T with X the trial's inverse Cholesky factor from the split-precision
+// factorisation; A is PD iff M is (congruence), and M = I - X E X^T where E is the
+// factorisation's backward error, so |M - I| is tiny for a PD trial and at least 1 for an
+// indefinite one.  Three FP64 power steps on M - I estimate its spectral radius.
+
+// part[b][j] = sum over rows i of block b (32 rows) of X[i][j] v[i], X lower triangular
+__global__ void k_tmatvec_part(const double* __restrict__ X, int64_t ld, int64_t n, const double* __restrict__ v,
+                               double* __restrict__ part) {
+  const int64_t b = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t r0 = b * 32, r1 = r0 + 32 < n ? r0 + 32 : n;
+  double s = 0.0;
+  for (int64_t i = (r0 > j ? r0 : j); i < r1; ++i) s = fma(X[i * ld + j], v[i], s);
+  part[b * n + j] = s;
+}
+// y[j] = sum over row blocks b (from the one holding row j on) of part[b][j], in order
+__global__ void k_sum_cols(const double* __restrict__ part, int64_t nb, int64_t n, double* __restrict__ y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int64_t b = j / 32; b < nb; ++b) s += part[b * n + j];
+  y[j] = s;
+}
+// y = X x for a lower-triangular X (one block per row, columns j <= i)
+__global__ void k_gemv_lower(const double* __restrict__ X, int64_t ld, int64_t n, const double* __restrict__ x,
+                             double* __restrict__ y) {
+  __shared__ double red[32];
+  const int64_t i = blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j <= i; j += blockDim.x) s = fma(X[i * ld + j], x[j], s);
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) y[i] = t;
+}
+// v <- (z - v) / |z - v|, *nrm = |z - v|
+__global__ void k_diff_normalize(const double* __restrict__ z, int64_t n, double* __restrict__ v, double* nrm) {
+  __shared__ double red[32];
+  __shared__ double tot;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double d = z[j] - v[j];
+    s = fma(d, d, s);
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) { tot = sqrt(t); *nrm = tot; }
+  __syncthreads();
+  const double inv = tot > 0.0 ? 1.0 / tot : 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = (z[j] - v[j]) * inv;
+}
+// a fixed start vector with entries in [-1, 1] (a multiplicative hash of the index), scaled
+// to unit length by the caller's first normalisation
+__global__ void k_start_vector(double* x, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    const uint32_t h = (uint32_t)(j + 1) * 2654435761u;
+    x[j] = (double)h / 2147483648.0 - 1.0;
+  }
+}
+
 // CSR capacity of the sparse sandwich: 256 nonzeros per row on average
 int64_t csr_cap(int np) { return (int64_t)256 * np; }
 
@@ -63,7 +123,9 @@ void dfree(T*& p) {
 size_t Workspace::bytes_for(int np) {
   const size_t m = (size_t)np * np;
   const size_t csr = (size_t)(np + 1) * 8 + (size_t)np * 4 + (size_t)csr_cap(np) * 12;
-  return 11 * m * sizeof(double) + m + tc_scratch_bytes_for(np) + csr;
+  // 11 FP64 matrices, the int8 code, the tensor-core operand splits, the CSR, and the staging
+  // buffer of a host input (up to np^2 FP64)
+  return 12 * m * sizeof(double) + m + tc_scratch_bytes_for(np) + csr;
 }
 
 void Workspace::release() {
@@ -188,9 +250,11 @@ Profiler::~Profiler() {
 }
 
 namespace {
-// algorithmic FLOPs of one product with the structure the call declares
-double gemm_flops(const GemmArgs& a) {
-  const double M = a.M, N = a.N, K = a.K;
+// algorithmic FLOPs of one product with the structure the call declares; a dimension that
+// spans the whole padded matrix (np) counts as the problem's n
+double gemm_flops(const GemmArgs& a, int np, int64_t n) {
+  auto alg = [&](int d) { return d == np ? (double)n : (double)d; };
+  const double M = alg(a.M), N = alg(a.N), K = alg(a.K);
   switch (a.krule) {
     case KR_LO_COL: return M * N * (N + 1.0);                 // B lower triangular (K = N)
     case KR_HI_ROW: return N * M * (M + 1.0);                 // A lower triangular (K = M)
@@ -244,7 +308,7 @@ Engine::~Engine() {
 
 void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
   Profiler::Rec rec;
-  prof.begin_rec(prof_class(role), gemm_flops(a), st, rec);
+  prof.begin_rec(prof_class(role), gemm_flops(a, ws.np, ws.n), st, rec);
   const bool mixed = cfg_.precision != GLASSO_FP64;
   if (mixed && gemm_f32_supported(a)) {
     gemm_f32(a, st);
@@ -312,8 +376,10 @@ void Engine::load_matrix(const void* src, bool f32, bool on_device, int64_t n, d
 void Engine::factor_direct(double* L, double* Li, cudaStream_t st) {
   k_set_int<<<1, 1, 0, st>>>(ws.pd, 1);
   LAUNCH_CHECK();
-  cholesky_inverse(L, Li, ws.ld, ws.np, ws.T, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st,
-                   cfg_.precision != GLASSO_FP64, panel_);
+  const bool split = cfg_.precision != GLASSO_FP64;
+  const LeafKind kind = !split ? LeafKind::F64 : cfg_.fp32_panels ? LeafKind::F32 : LeafKind::F64Chol;
+  cholesky_inverse(L, Li, ws.ld, ws.np, ws.T, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st, split, kind,
+                   panel_);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
 }
 
@@ -331,7 +397,7 @@ void Engine::factor(double* L, double* Li, cudaStream_t st) {
   // profiling times a replayed graph as one FACTOR record (its launches cannot carry events);
   // before a graph exists the direct launches are recorded class by class
   Profiler::Rec rec;
-  const double np3 = (double)ws.np * ws.np * ws.np;
+  const double np3 = (double)ws.n * ws.n * ws.n;  // algorithmic: n^3 / 3 + n^3 / 3 on n
   if (graph_epoch_ != ws.epoch) {
     drop_graphs();
     graph_epoch_ = ws.epoch;
@@ -395,7 +461,7 @@ void Engine::compute_inverse(double* Li, cudaStream_t st) {
   inverse_from_inverse_factor(Li, ws.ld, ws.np, ws.W, gemm_fn(), st);
   {
     Profiler::Rec rec;
-    prof.begin_rec(GLASSO_PROF_AUX, 8.0 * (double)ws.np * (double)ws.np, st, rec);
+    prof.begin_rec(GLASSO_PROF_AUX, 8.0 * (double)ws.n * (double)ws.n, st, rec);
     mirror_lower(ws.W, ws.ld, ws.np, st);
     prof.end_rec(rec, st);
   }
@@ -413,7 +479,7 @@ void Engine::refine_inverse(cudaStream_t st) {
   const int np = ws.np;
   const int64_t ld = ws.ld;
   double* rmax = &ws.sc->aux[0];
-  const double nn = (double)np * (double)np;
+  const double nn = (double)ws.n * (double)ws.n;  // algorithmic bytes count the n x n block
   const double c = cfg_.precision == GLASSO_MIXED_BF16X3 ? 3e-5 : 1e-6;
   for (int sweep = 0; sweep < 3; ++sweep) {
     {
@@ -504,17 +570,50 @@ void Engine::sandwich(double nnz, cudaStream_t st) {
   gemm(b, GemmRole::Sandwich, st);
 }
 
-double Engine::power_lambda_max(const double* M, cudaStream_t st) {
+double Engine::power_lambda_max(const double* M, cudaStream_t st, int iters) {
   const int64_t n = ws.n;
   double* x = ws.vec;
   double* y = ws.vec + ws.np;
   double* nrm = ws.vec + 2 * ws.np;
   k_fill<<<(int)((n + 255) / 256), 256, 0, st>>>(x, n, 1.0 / std::sqrt((double)n));
   LAUNCH_CHECK();
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < iters; ++it) {
     k_gemv_rows<<<(int)n, 256, 0, st>>>(M, ws.ld, n, x, y);
     LAUNCH_CHECK();
     k_normalize<<<1, 1024, 0, st>>>(y, n, x, nrm);
+    LAUNCH_CHECK();
+  }
+  double h = 0.0;
+  CUDA_CHECK(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return h;
+}
+
+// Spectral radius estimate of M - I, M = X A X^T (X = the trial's inverse factor Lti, A the
+// trial point At), from three FP64 power steps; see k_tmatvec_part.  Uses ws.T as scratch.
+double Engine::congruence_radius(cudaStream_t st) {
+  const int64_t n = ws.n, ld = ws.ld;
+  const int64_t nb = (n + 31) / 32;
+  double* v = ws.vec;
+  double* u = ws.vec + ws.np;
+  double* z = ws.vec + 2 * ws.np;
+  double* nrm = &ws.sc->aux[4];
+  const unsigned g = (unsigned)((n + 255) / 256);
+  k_start_vector<<<g, 256, 0, st>>>(z, n);
+  LAUNCH_CHECK();
+  CUDA_CHECK(cudaMemsetAsync(v, 0, sizeof(double) * n, st));
+  k_diff_normalize<<<1, 1024, 0, st>>>(z, n, v, nrm);  // v = z / |z|
+  LAUNCH_CHECK();
+  for (int it = 0; it < 3; ++it) {
+    k_tmatvec_part<<<dim3(g, (unsigned)nb), 256, 0, st>>>(ws.Lti, ld, n, v, ws.T);   // X^T v
+    LAUNCH_CHECK();
+    k_sum_cols<<<g, 256, 0, st>>>(ws.T, nb, n, u);
+    LAUNCH_CHECK();
+    k_gemv_rows<<<(unsigned)n, 256, 0, st>>>(ws.At, ld, n, u, z);                     // A X^T v
+    LAUNCH_CHECK();
+    k_gemv_lower<<<(unsigned)n, 256, 0, st>>>(ws.Lti, ld, n, z, u);                   // X A X^T v
+    LAUNCH_CHECK();
+    k_diff_normalize<<<1, 1024, 0, st>>>(u, n, v, nrm);                               // (M - I) v
     LAUNCH_CHECK();
   }
   double h = 0.0;
@@ -531,6 +630,7 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   const int np = ws.np;
   const int64_t ld = ws.ld;
@@ -586,7 +686,8 @@ int Engine::gista_step(double tol, int max_iter, bool keep_trace) {
   Scalars& h = *ws.hs;
   SolveOut& out = st_.out;
   csr_valid_ = false;
-  compute_inverse(ws.Li, st);
+  if (!w_valid_) compute_inverse(ws.Li, st);
+  w_valid_ = true;
   {
     Profiler::Rec rec;
     prof.begin_rec(GLASSO_PROF_GRADIENT, 33.0 * (double)n * (double)n, st, rec);
@@ -599,7 +700,7 @@ int Engine::gista_step(double tol, int max_iter, bool keep_trace) {
   out.nnz = h.nnz;
   if (out.r <= tol) return GLASSO_OK;
   if (st_.k >= max_iter) return GLASSO_MAX_ITER;
-  const double lmax_w = power_lambda_max(ws.W, st);
+  const double lmax_w = power_lambda_max(ws.W, st, 60);
   const double t_safe = 0.5 / (lmax_w * lmax_w);
   const double f = -st_.ld_A + st_.trsa;
   double t = std::min(1.0, std::max(2.0 * st_.t_last, t_safe));
@@ -641,6 +742,7 @@ int Engine::gista_step(double tol, int max_iter, bool keep_trace) {
   std::swap(ws.A, ws.At);
   std::swap(ws.L, ws.Lt);
   std::swap(ws.Li, ws.Lti);
+  w_valid_ = false;
   st_.ld_A = h.logdet_t;
   st_.trsa = h.gista[0];
   st_.l1 = h.gista[1];
@@ -663,7 +765,8 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   const double t_min = cfg_.t_min > 0 ? cfg_.t_min : 1e-4;
 
   csr_valid_ = false;  // A changed since the last step (or the CSR holds a difference)
-  compute_inverse(ws.Li, st);
+  if (!w_valid_) compute_inverse(ws.Li, st);
+  w_valid_ = true;
   {
     Profiler::Rec rec;
     prof.begin_rec(GLASSO_PROF_GRADIENT, 33.0 * (double)n * (double)n, st, rec);
@@ -710,6 +813,17 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
         tier = 2;
       }
     }
+    // Split-precision forms: the Cholesky pivots decide PD for the matrix the factorisation
+    // saw, which differs from At by the split products' error.  A step about to be accepted
+    // is therefore certified PD in FP64: by |E|_F <= 0.1 < 1 when tier 2 decided (At = A^{1/2}
+    // (I + E) A^{1/2} with A PD), else by the congruence X At X^T = I + F with |F| < 1/2.
+    if (d < 0.0 && tier == 1 && cfg_.precision != GLASSO_FP64) {
+      ++out.pd_checks;
+      if (!(congruence_radius(st) < 0.5)) {
+        ++out.pd_refused;
+        return INFINITY;
+      }
+    }
     return d;
   };
   while (t >= t_min) {
@@ -720,8 +834,11 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   bool fallback = false;
   if (!accepted) {
     fallback = true;
-    const double lmax_a = power_lambda_max(ws.A, st);
-    const double lmax_w = power_lambda_max(ws.W, st);
+    // cond_2 = lambda_max(A) lambda_max(W); power iteration underestimates both, and the
+    // fallback step is an upper bound in Sec. 6, so it runs long enough (300 steps) to bring
+    // the estimate within rounding on the spectra of the paper's workloads
+    const double lmax_a = power_lambda_max(ws.A, st, 300);
+    const double lmax_w = power_lambda_max(ws.W, st, 300);
     t = std::pow(kFallbackFactor / (lmax_a * lmax_w), 2.0);
     dF = try_step(t);
     accepted = dF < 0.0;
@@ -737,6 +854,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   std::swap(ws.A, ws.At);
   std::swap(ws.L, ws.Lt);
   std::swap(ws.Li, ws.Lti);
+  w_valid_ = false;
   st_.ld_A = h.logdet_t;
   st_.trsa = h.trsa_t;
   st_.l1 = h.l1_t;
@@ -781,12 +899,86 @@ SolveOut Engine::solve(const void* Sin, bool s_f32, bool s_on_device, int64_t n,
 }
 
 // ------------------------------------------------------------------------------------------
+// device-resident states (serving: warm starts without the start point's factorisation)
+// ------------------------------------------------------------------------------------------
+void Engine::begin_resident(const void* Sin, bool s_f32, int64_t n, double lam, const Resident& r) {
+  if (r.n != n || !r.theta || !r.li || !r.w) throw Error(GLASSO_ERR_ARG, "resident state of another size");
+  st_ = SolveState{};
+  st_.t_begin = std::chrono::steady_clock::now();
+  st_.launches_begin = tl_launches;
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  ws.ensure(n, cfg_.hbm_budget_bytes);
+  if (r.np != ws.np) throw Error(GLASSO_ERR_ARG, "resident state of another padded size");
+  csr_valid_ = false;
+  cudaStream_t st = stream_;
+  const size_t mat = sizeof(double) * ws.ld * ws.np;
+  load_matrix(Sin, s_f32, false, n, ws.S, true);
+  if (cfg_.standardize) {
+    int bad = 0;
+    CUDA_CHECK(cudaMemsetAsync(ws.bad, 0, sizeof(int), st));
+    standardize(ws.S, ws.ld, n, ws.vec, ws.bad, st);
+    CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (bad) throw Error(GLASSO_ERR_ARG, "standardize needs every S_ii > 0");
+  }
+  CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ws.ld * ws.np, st));
+  CUDA_CHECK(cudaMemcpyAsync(ws.A, r.theta, mat, cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(ws.Li, r.li, mat, cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(ws.W, r.w, mat, cudaMemcpyDeviceToDevice, st));
+  objective_terms(ws.S, ws.A, ws.ld, n, ws.parts, &ws.sc->trsa, st);
+  sync_scalars();
+  w_valid_ = true;
+  st_.active = true;
+  st_.on_device = false;
+  st_.n = n;
+  st_.lam = lam;
+  st_.ld_A = r.logdet;
+  st_.trsa = ws.hs->trsa;
+  st_.l1 = ws.hs->l1;
+  st_.F = -st_.ld_A + st_.trsa + lam * st_.l1;
+}
+
+double Engine::export_resident(double* theta, double* li, double* w) {
+  if (!w_valid_) throw Error(GLASSO_ERR_ARG, "no current inverse to export");
+  cudaStream_t st = stream_;
+  const size_t mat = sizeof(double) * ws.ld * ws.np;
+  CUDA_CHECK(cudaMemcpyAsync(theta, ws.A, mat, cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(li, ws.Li, mat, cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(w, ws.W, mat, cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return st_.ld_A;
+}
+
+SolveOut Engine::solve_resident(const void* Sin, bool s_f32, int64_t n, double lam, double tol, const Resident& r,
+                                double* theta_out) {
+  const int max_iter = cfg_.max_iter > 0 ? cfg_.max_iter : 500;
+  begin_resident(Sin, s_f32, n, lam, r);
+  int status;
+  while ((status = step(tol, max_iter, false)) < 0) {
+  }
+  SolveOut out = finish(theta_out);
+  out.status = status;
+  return out;
+}
+
+void Engine::release_workspace() {
+  CUDA_CHECK(cudaSetDevice(cfg_.device));
+  if (stream_) CUDA_CHECK(cudaStreamSynchronize(stream_));
+  drop_graphs();
+  ws.release();
+  csr_valid_ = false;
+  w_valid_ = false;
+  st_.active = false;
+}
+
+// ------------------------------------------------------------------------------------------
 // single steps
 // ------------------------------------------------------------------------------------------
 void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.Lt, false);
   pad_identity(ws.Lt, ws.ld, n, ws.np, st);
@@ -802,6 +994,7 @@ int Engine::op_inverse(const double* A, int64_t n, double* W) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   pad_identity(ws.A, ws.ld, n, ws.np, st);
@@ -820,6 +1013,7 @@ void Engine::op_gradient(const double* S, const double* A, const double* W, int6
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(S, false, true, n, ws.S, false);
   load_matrix(A, false, true, n, ws.A, false);
@@ -835,6 +1029,7 @@ void Engine::op_sandwich(const double* A, const double* X, int64_t n, double* Y)
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   load_matrix(X, false, true, n, ws.X, false);
@@ -854,6 +1049,7 @@ void Engine::op_trial(const double* A, const double* Y, const int8_t* code, int6
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
   csr_valid_ = false;
+  w_valid_ = false;
   cudaStream_t st = stream_;
   load_matrix(A, false, true, n, ws.A, false);
   load_matrix(Y, false, true, n, ws.Y, false);

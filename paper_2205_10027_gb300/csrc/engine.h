@@ -58,6 +58,8 @@ struct SolveOut {
   // the last line search: its final trial step, dF, tier and whether the fallback ran
   double step_t = 0, step_dF = 0;
   int step_tier = 0, step_fallback = 0;
+  // split-precision forms: FP64 PD certificates run on trial points, and trials they refused
+  int pd_checks = 0, pd_refused = 0;
   std::vector<IterRecord> trace;
 };
 
@@ -108,6 +110,28 @@ class Engine {
   // Returns -1 after an accepted step, else the final status (OK, MAX_ITER, STALL).
   int step(double tol, int max_iter, bool keep_trace);
   SolveOut finish(double* theta_out);
+
+  // Device-resident solver state: an iterate Theta, the inverse of its Cholesky factor and
+  // W = Theta^{-1}, each np x np (leading dimension np, the workspace layout), and log det.
+  struct Resident {
+    int64_t n = 0;
+    int np = 0;
+    const double* theta = nullptr;
+    const double* li = nullptr;
+    const double* w = nullptr;
+    double logdet = 0.0;
+  };
+  // Start a solve from a resident state of the same n (a warm start that skips the start
+  // point's factorisation and the first inverse); S as for begin (host memory).
+  void begin_resident(const void* S, bool s_f32, int64_t n, double lam, const Resident& r);
+  // Copy the current iterate, its inverse factor and W into resident buffers (np x np each)
+  // and return log det; valid after a solve ended (W is then the current iterate's inverse).
+  double export_resident(double* theta, double* li, double* w);
+  // A full solve started from a resident state (begin_resident + steps + finish).
+  SolveOut solve_resident(const void* S, bool s_f32, int64_t n, double lam, double tol, const Resident& r,
+                          double* theta_out);
+  // Give the device workspace back (the next solve allocates it again).
+  void release_workspace();
   const SolveState& state() const { return st_; }
   Profiler prof;
 
@@ -135,13 +159,15 @@ class Engine {
   // exceeds the capacity
   bool ensure_csr_of_A(cudaStream_t st);
   bool csr_valid_ = false;
+  bool w_valid_ = false;  // ws.W holds the inverse of ws.A (refined in the split-precision forms)
   // Q = (At - A) W and {tr Q, tr Q^2} into the scalars
   void logdet_terms(double nnz_bound, cudaStream_t st);
   void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);
   int gista_step(double tol, int max_iter, bool keep_trace);
-  double power_lambda_max(const double* M, cudaStream_t st);
+  double power_lambda_max(const double* M, cudaStream_t st, int iters);
+  double congruence_radius(cudaStream_t st);
   void sync_scalars();
 
   // CUDA graphs of the factorisation, one per (factor buffer, inverse buffer) pair

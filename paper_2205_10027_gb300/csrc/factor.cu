@@ -3,9 +3,11 @@
 // eq. sparse_obj), and W = A^{-1} = X^T X from X = L^{-1} (eq. grad_hessian needs W).
 //
 // Splitting the matrix in halves puts almost all of the work in a few large products
-// (K up to np/2), which is what the tensor cores need; the leaves are 64 x 64 (FP64) or
-// 128 x 128 (FP32, split-precision modes) blocks that one CTA factors and inverts.  Layout: np x np row-major, np a multiple of 128; the factor
-// overwrites the lower triangle of A in place, X is written in full (zero upper).
+// (K up to np/2), which is what the tensor cores need; the leaves are diagonal blocks that one
+// CTA factors and inverts: 64 x 64 in FP64 (the FP64 form), 64 x 64 with an FP64 Cholesky and
+// an FP32 inverse (the split-precision forms), or, as an option of the split-precision forms,
+// 128 x 128 in FP32.  Layout: np x np row-major, np a multiple of 128; the factor overwrites
+// the lower triangle of A in place, X is written in full (zero upper).
 #include <mutex>
 #include "factor.h"
 
@@ -240,6 +242,239 @@ __global__ void __launch_bounds__(PT) k_leaf_chol_inv(double* Ablk, int64_t ld, 
 // dynamic shared memory of k_leaf_chol_inv: two NB x (NB + 4) arrays
 constexpr size_t leaf_smem(int nb, size_t elt) { return 2 * (size_t)nb * (nb + 4) * elt; }
 
+// ---- 128 x 128 leaf of the split-precision forms: FP64 Cholesky panels, FP32 inverse ----
+// The diagonal block is factored as two 64 x 64 FP64 Cholesky panels (the pivots, the PD test
+// and the log det are FP64 arithmetic on the FP64 Schur complement) joined inside the CTA by
+// the block's own small products: L21 = A21 X11^T and X21 = -X22 (L21 X11) in FP32 (the
+// accuracy of the split-precision products they stand beside), and the trailing update
+// A22 -= L21 L21^T formed in FP32 and subtracted from the FP64 A22 in FP64.  The inverse
+// X = L^{-1}, which only feeds split-precision products, is formed in FP32.
+//
+// On this part the FP64 pipe issues one warp instruction per 64 cycles per sub-partition and
+// an FP64 divide takes ~430 cycles, so each FP64 panel keeps its serial chain short: the
+// right-looking update is kept unscaled (a_ic -= a_ij a_cj / d_j, L recovered at the end as
+// a_ij / sqrt(d_j)), one lane of warp 0 runs the pivot chain d_{j+1} = a_{j+1,j+1} -
+// a_{j+1,j}^2 / d_j one column ahead, and the six warps on the other three sub-partitions
+// apply the update of column j to the rest of the trailing triangle meanwhile.
+constexpr int L64 = 64, L64P = 65;     // panel size, shared row pitch (odd: conflict-free columns)
+constexpr int LEAF128_THREADS = 256;
+constexpr size_t leaf128_smem() {
+  return 3 * (size_t)L64 * L64P * sizeof(double) + 5 * (size_t)L64 * L64P * sizeof(float);
+}
+
+// FP64 Cholesky of the 64 x 64 lower triangle in a (pitch L64P), all 256 threads.  On return a
+// holds L (lower), piv[j] = L_jj^2, and *fail != 0 on a pivot that is not finite and positive.
+// inv and tcol are 64-entry shared scratch.
+__device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, int* fail) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // update warps: the six on sub-partitions 1-3 (warp w runs on w % 4); warp 0 runs the chain
+  const int uw = warp == 1 ? 0 : warp == 2 ? 1 : warp == 3 ? 2 : warp == 5 ? 3 : warp == 6 ? 4 : warp == 7 ? 5 : -1;
+  if (tid == 0) {
+    const double d = a[0];
+    if (!(d > 0.0) || isinf(d)) *fail = 1;
+    piv[0] = d;
+    inv[0] = 1.0 / d;
+  }
+  __syncthreads();
+  for (int j = 0; j < L64; ++j) {
+    if (*fail) break;
+    if (tid == 0 && j + 1 < L64) {
+      // the pivot chain, one column ahead: every update of a_{j+1,j} and a_{j+1,j+1} from
+      // columns < j is in place (previous steps)
+      const double aj = a[(j + 1) * L64P + j];
+      const double d = fma(-aj * inv[j], aj, a[(j + 1) * L64P + j + 1]);
+      if (!(d > 0.0) || isinf(d)) *fail = 1;
+      a[(j + 1) * L64P + j + 1] = d;
+      piv[j + 1] = d;
+      inv[j + 1] = 1.0 / d;
+    } else if (uw >= 0) {
+      // t_i = a_ij / d_j for the rows below, then a_ic -= t_i a_cj for c > j, i >= c, except
+      // the diagonal entry (j+1, j+1), which the chain has updated
+      if (uw < 2) {
+        const int i = j + 1 + 32 * uw + lane;
+        if (i < L64) tcol[i] = a[i * L64P + j] * inv[j];
+      }
+      asm volatile("bar.sync 1, 192;" ::: "memory");
+      for (int c = j + 1 + uw; c < L64; c += 6) {
+        const double acj = a[c * L64P + j];
+        for (int i = c + (c == j + 1 ? 1 : 0) + lane; i < L64; i += 32)
+          a[i * L64P + c] = fma(-tcol[i], acj, a[i * L64P + c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (*fail) return;
+  // L_ij = a_ij / sqrt(d_j) (i > j), L_jj = sqrt(d_j)
+  if (tid < L64) tcol[tid] = rsqrt(piv[tid]);
+  __syncthreads();
+  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    if (c <= i) a[i * L64P + c] = (c == i ? piv[c] : a[i * L64P + c]) * tcol[c];
+  }
+  __syncthreads();
+}
+
+// X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch L64P): thread c
+// (< 64) forms column c by forward substitution, x_ic = (delta_ic - sum_{k<i} l_ik x_kc) / l_ii,
+// with the column held in registers (rows above c come out 0) and four partial sums per row.
+__device__ void trinv64_f32(const float* l, float* x) {
+  const int c = threadIdx.x;
+  if (c >= L64) return;
+  float xr[L64];
+#pragma unroll
+  for (int i = 0; i < L64; ++i) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < i; ++k) s[k & 3] = fmaf(l[i * L64P + k], xr[k], s[k & 3]);
+    xr[i] = ((i == c ? 1.f : 0.f) - ((s[0] + s[1]) + (s[2] + s[3]))) / l[i * L64P + i];
+  }
+#pragma unroll
+  for (int i = 0; i < L64; ++i) x[i * L64P + c] = xr[i];
+}
+
+// acc (4 x 4 block at rows r0, columns c0) = sum_k A(i, k) B(k, j) over k < 64, A(i, k) at
+// a[i * L64P + k]; B(k, j) at b[k * L64P + j], or at b[j * L64P + k] when BT (a transpose).
+template <bool BT>
+__device__ __forceinline__ void mm64_4x4(const float* a, const float* b, int r0, int c0, float (&acc)[4][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < L64; ++k) {
+    float av[4], bv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) av[q] = a[(r0 + q) * L64P + k];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) bv[p] = BT ? b[(c0 + p) * L64P + k] : b[k * L64P + c0 + p];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(av[q], bv[p], acc[q][p]);
+  }
+}
+
+__global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64_t ld, double* Xblk, double* ld_part,
+                                                         int* pd) {
+  if (*pd == 0) return;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int M = L64 * L64P;
+  double* a11 = reinterpret_cast<double*>(sm_raw);  // FP64 panels: A11 -> L11, A21 -> L21, A22 -> L22
+  double* a21 = a11 + M;
+  double* a22 = a21 + M;
+  float* f0 = reinterpret_cast<float*>(a22 + M);    // L11 (FP32), then L21 (FP32)
+  float* f1 = f0 + M;                                // X11
+  float* f2 = f1 + M;                                // A21 (FP32), then L22 (FP32), then X21
+  float* f3 = f2 + M;                                // X22
+  float* f4 = f3 + M;                                // T = L21 X11
+  __shared__ double piv[2 * L64], inv[L64], tcol[L64];
+  __shared__ double red[32];
+  __shared__ int fail;
+  const int tid = threadIdx.x;
+  const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;  // 4 x 4 output block of the small products
+  for (int e = tid; e < 2 * L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;   // i < 128: rows of the block's left column panel
+    const double v = (c <= i) ? Ablk[(int64_t)i * ld + c] : 0.0;
+    if (i < L64) a11[i * L64P + c] = v;
+    else a21[(i - L64) * L64P + c] = v;
+  }
+  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    a22[i * L64P + c] = (c <= i) ? Ablk[(int64_t)(L64 + i) * ld + L64 + c] : 0.0;
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  // ---- first panel: L11 (FP64), X11 = L11^{-1} (FP32)
+  chol64_f64(a11, piv, inv, tcol, &fail);
+  if (fail) {
+    if (tid == 0) *pd = 0;
+    return;
+  }
+  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    f0[i * L64P + c] = f64_to_f32(a11[i * L64P + c]);
+    f2[i * L64P + c] = f64_to_f32(a21[i * L64P + c]);
+  }
+  __syncthreads();
+  trinv64_f32(f0, f1);
+  __syncthreads();
+  // ---- L21 = A21 X11^T (FP32), kept in FP64 (a21) and FP32 (f0)
+  {
+    float acc[4][4];
+    mm64_4x4<true>(f2, f1, r0, c0, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        a21[(r0 + q) * L64P + c0 + p] = f32_to_f64(acc[q][p]);
+        f0[(r0 + q) * L64P + c0 + p] = acc[q][p];
+      }
+  }
+  __syncthreads();
+  // ---- A22 -= L21 L21^T: FP32 product, FP64 subtraction (lower triangle)
+  {
+    float acc[4][4];
+    mm64_4x4<true>(f0, f0, r0, c0, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        if (c0 + p <= r0 + q) a22[(r0 + q) * L64P + c0 + p] -= f32_to_f64(acc[q][p]);
+  }
+  // ---- T = L21 X11 (FP32), independent of the second panel
+  {
+    float acc[4][4];
+    mm64_4x4<false>(f0, f1, r0, c0, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) f4[(r0 + q) * L64P + c0 + p] = acc[q][p];
+  }
+  __syncthreads();
+  // ---- second panel: L22 (FP64), X22 (FP32)
+  chol64_f64(a22, piv + L64, inv, tcol, &fail);
+  if (fail) {
+    if (tid == 0) *pd = 0;
+    return;
+  }
+  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    f2[i * L64P + c] = f64_to_f32(a22[i * L64P + c]);
+  }
+  __syncthreads();
+  trinv64_f32(f2, f3);
+  __syncthreads();
+  // ---- X21 = -X22 T (FP32)
+  {
+    float acc[4][4];
+    mm64_4x4<false>(f3, f4, r0, c0, acc);
+    __syncthreads();  // every thread has read f2 (L22) before it is overwritten
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) f2[(r0 + q) * L64P + c0 + p] = -acc[q][p];
+  }
+  // ---- log det = sum of log pivots (FP64)
+  const double lsum = (tid < 2 * L64) ? log(piv[tid]) : 0.0;
+  const double tot = block_sum(lsum, red);   // its barriers also order the writes above
+  __syncthreads();
+  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    double* Ar0 = Ablk + (int64_t)i * ld;
+    double* Ar1 = Ablk + (int64_t)(L64 + i) * ld;
+    double* Xr0 = Xblk + (int64_t)i * ld;
+    double* Xr1 = Xblk + (int64_t)(L64 + i) * ld;
+    Ar0[c] = (c <= i) ? a11[i * L64P + c] : 0.0;   // L11 (zero upper)
+    Ar0[L64 + c] = 0.0;                            // upper off-diagonal block
+    Ar1[c] = a21[i * L64P + c];                    // L21
+    Ar1[L64 + c] = (c <= i) ? a22[i * L64P + c] : 0.0;   // L22
+    if (c <= i) Xr0[c] = f32_to_f64(f1[i * L64P + c]);   // X11
+    Xr1[c] = f32_to_f64(f2[i * L64P + c]);                // X21
+    if (c <= i) Xr1[L64 + c] = f32_to_f64(f3[i * L64P + c]);   // X22
+  }
+  if (tid == 0) *ld_part = tot;
+}
+
 // out = sum of parts[0..n) in index order (one thread: n is at most a few hundred).
 __global__ void k_sum_parts(const double* parts, int n, const int* pd, double* out) {
   if (threadIdx.x != 0) return;
@@ -273,7 +508,8 @@ __global__ void k_mirror_lower(double* M, int64_t ld, int np) {
 
 namespace {
 struct Ctx {
-  bool fp32_leaf;  // split-precision modes: FP32 leaves of NB32 rows, in-place panel products
+  bool split;      // split-precision modes: in-place panel products on the tensor cores
+  LeafKind kind;   // which leaf kernel factors the diagonal blocks
   int leaf;
   double* A;
   double* X;
@@ -293,10 +529,17 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
   if (s == c.leaf) {
     double* Ab = c.A + (int64_t)o * c.ld + o;
     double* Xb = c.X + (int64_t)o * c.ld + o;
-    if (c.fp32_leaf)
-      k_leaf_chol_inv<float, NB32, 4 * NB32><<<1, 4 * NB32, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
-    else
-      k_leaf_chol_inv<double, NB, 4 * NB><<<1, 4 * NB, c.smem, c.st>>>(Ab, c.ld, Xb, c.ld_parts + o / c.leaf, c.pd);
+    double* part = c.ld_parts + o / c.leaf;
+    switch (c.kind) {
+      case LeafKind::F64Chol:
+        k_leaf128<<<1, LEAF128_THREADS, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+        break;
+      case LeafKind::F32:
+        k_leaf_chol_inv<float, NB32, 4 * NB32><<<1, 4 * NB32, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+        break;
+      default:
+        k_leaf_chol_inv<double, NB, 4 * NB><<<1, 4 * NB, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+    }
     LAUNCH_CHECK();
     return;
   }
@@ -312,7 +555,7 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
   // from the split copies made before it starts, so it may overwrite A21 in place; the
   // CUDA-core kernels (FP64, and FP32 for small products) read A21 tile by tile and go
   // through T.
-  const bool in_place = c.fp32_leaf && std::max(s1, s2) > kSmallGemm;
+  const bool in_place = c.split && std::max(s1, s2) > kSmallGemm;
   GemmArgs a = gemm_args(A21, ld, 0, X11, ld, 1, in_place ? A21 : c.T, ld, s2, s1, s1, 1.0, 0.0);
   a.krule = KR_HI_COL;
   a.flag = c.pd;
@@ -340,9 +583,12 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
 }  // namespace
 
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
-                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf, int panel) {
-  const int leaf = fp32_leaf ? NB32 : NB;
-  const size_t smem = leaf_smem(leaf, fp32_leaf ? sizeof(float) : sizeof(double));
+                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool split, LeafKind kind,
+                      int panel) {
+  const int leaf = kind == LeafKind::F64 ? NB : NB32;
+  const size_t smem = kind == LeafKind::F64Chol ? leaf128_smem()
+                      : kind == LeafKind::F32   ? leaf_smem(NB32, sizeof(float))
+                                                : leaf_smem(NB, sizeof(double));
   static std::once_flag once;  // not repeated inside a stream capture
   std::call_once(once, [] {
     CUDA_CHECK(cudaFuncSetAttribute(k_leaf_chol_inv<float, NB32, 4 * NB32>,
@@ -351,9 +597,10 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
     CUDA_CHECK(cudaFuncSetAttribute(k_leaf_chol_inv<double, NB, 4 * NB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)leaf_smem(NB, sizeof(double))));
+    CUDA_CHECK(cudaFuncSetAttribute(k_leaf128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf128_smem()));
   });
   CUDA_CHECK(cudaMemsetAsync(X, 0, sizeof(double) * ld * np, st));
-  Ctx c{fp32_leaf, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem};
+  Ctx c{split, kind, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem};
   if (panel <= 0) {
     chol_inv_rec(c, 0, np);
   } else {
@@ -368,11 +615,11 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
       double* A21 = A + (int64_t)(o + s) * ld + o;
       double* A22 = A + (int64_t)(o + s) * ld + o + s;
       const double* Xkk = X + (int64_t)o * ld + o;
-      GemmArgs a = gemm_args(A21, ld, 0, Xkk, ld, 1, fp32_leaf ? A21 : T, ld, rem, s, s, 1.0, 0.0);
+      GemmArgs a = gemm_args(A21, ld, 0, Xkk, ld, 1, split ? A21 : T, ld, rem, s, s, 1.0, 0.0);
       a.krule = KR_HI_COL;
       a.flag = pd;
       gemm(a, GemmRole::Panel, st);
-      if (!fp32_leaf) {
+      if (!split) {
         k_copy_block<<<std::min(rem, 1024), 256, 0, st>>>(T, A21, ld, rem, s, pd);
         LAUNCH_CHECK();
       }

@@ -17,11 +17,17 @@ using GemmFn = std::function<void(const GemmArgs&, GemmRole, cudaStream_t)>;
 // block factored recursively; X then holds only the inverses of the diagonal panel blocks
 // (inverse_merge completes it).  T is np x np scratch.  *pd must be 1 on entry and is
 // cleared on a bad pivot, after which the remaining launches do nothing; *logdet =
-// 2 sum log L_ii (NaN when not PD).  ld_parts: np/64 doubles.  fp32_leaf: the leaf blocks are
-// factored and inverted in FP32 arithmetic (split-precision modes).
+// 2 sum log L_ii (NaN when not PD).  ld_parts: np/64 doubles.  split: the products run in a
+// split-precision mode (the tensor-core panel products may then write their output in place).
+// kind: the leaf kernel of the diagonal blocks.
+enum class LeafKind {
+  F64,      // 64 x 64, Cholesky and inverse in FP64 (the FP64 form)
+  F64Chol,  // 64 x 64, Cholesky, pivots and log det in FP64, inverse of the factor in FP32
+  F32       // 128 x 128, Cholesky and inverse in FP32 (an option of the split-precision forms)
+};
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
-                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool fp32_leaf = false,
-                      int panel = 0);
+                      double* logdet, const GemmFn& gemm, cudaStream_t st, bool split = false,
+                      LeafKind kind = LeafKind::F64, int panel = 0);
 
 // Completes X = L^{-1} from the inverses of the diagonal panel blocks left by
 // cholesky_inverse(..., panel).  T is np x np scratch.

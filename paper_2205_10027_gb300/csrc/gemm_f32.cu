@@ -5,7 +5,7 @@
 // launch, TMEM allocation, pipeline fill, epilogue), while the CUDA cores finish it in a few
 // microseconds.  FP64 operands are converted to FP32 when staged in shared memory (integer
 // conversion), products accumulate in FP32 - the accuracy of the split products they
-// replace - and the result is stored in FP64.  Same structure options as the other GEMMs
+// replace - and the result is stored in FP64 (added to an FP64 C in FP64 when beta != 0).  Same structure options as the other GEMMs
 // (transposes, lower-triangle output, k-ranges of triangular operands, failure flag).
 #include <mutex>
 #include "gemm.h"
@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmAr
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
-  const float al = (float)p.alpha, be = (float)p.beta;
+  // alpha acc in FP32; a beta != 0 update (the factorisation's trailing updates) is added to
+  // the FP64 C in FP64, so the Schur complement loses nothing beyond the product's own error
+  const float al = (float)p.alpha;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = row0 + ty + 16 * i;
@@ -113,8 +115,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmAr
       const int c = col0 + tx + 16 * j;
       if (p.lower && c > r) continue;
       double* dst = p.C + (int64_t)r * p.ldc + c;
-      const float v = al * acc[i][j];
-      *dst = f32_to_f64(p.beta == 0.0 ? v : fmaf(be, f64_to_f32(*dst), v));
+      const double v = f32_to_f64(al * acc[i][j]);
+      *dst = p.beta == 0.0 ? v : fma(p.beta, *dst, v);
     }
   }
 }

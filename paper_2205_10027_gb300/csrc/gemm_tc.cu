@@ -2,7 +2,8 @@
 //
 // Each FP64 operand is split into hi + lo parts of a narrow type (TF32 or BF16); the product
 // op(A) op(B) is formed as hi*hi + hi*lo + lo*hi by tcgen05.mma with FP32 accumulation in
-// TMEM, and the epilogue writes alpha * acc + beta * C (FP32 arithmetic, FP64 storage).  One
+// TMEM, and the epilogue writes alpha * acc + beta * C (alpha * acc in FP32, the sum with the
+// FP64 C in FP64).  One
 // CTA computes a 128 x TN output tile: one thread issues TMA loads of the four operand tiles
 // of a k-stage (A_hi, A_lo: 128 rows; B_hi, B_lo: TN rows; KB bytes of K per row) into a
 // shared-memory ring, one thread issues the MMAs, and all warps drain the accumulator with
@@ -259,11 +260,13 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(p.err, 1);
   } else {
-    // FP32 arithmetic with integer conversions (the FP64 pipe is too narrow to spend two
-    // operations per output element); C stays FP64 in memory.  alpha and beta are 0 or +-1
-    // in every product of the solver, so only the beta != 0 update rounds, to FP32, which
-    // is the accuracy of the split products themselves.
-    const float al = (float)p.alpha, be = (float)p.beta;
+    // alpha * acc in FP32 (alpha is 0 or +-1 in every product of the solver), converted to
+    // FP64 by integer arithmetic; beta != 0 (the trailing updates A22 -= L21 L21^T of the
+    // factorisation) adds it to the FP64 C with one FP64 FMA, so the Schur complement keeps
+    // FP64 accuracy apart from the split product's own error.  That is one FP64 operation
+    // per output element of a K-long product: ~40 us of FP64 pipe per n = 10^4
+    // factorisation, spread over the whole GPU.
+    const float al = (float)p.alpha;
 #pragma unroll 1
     for (int c = c_first; c < c_end; ++c) {
       float v[32];
@@ -282,8 +285,8 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
         const int r = row0 + wq * 32 + rr;
         if (r >= p.M || col >= p.N || (p.lower && col > r)) continue;
         double* dst = p.C + (int64_t)r * p.ldc + col;
-        const float a = al * stage[rr * 33 + lane];
-        *dst = f32_to_f64(p.beta == 0.0 ? a : fmaf(be, f64_to_f32(*dst), a));
+        const double a = f32_to_f64(al * stage[rr * 33 + lane]);
+        *dst = p.beta == 0.0 ? a : fma(p.beta, *dst, a);
       }
       __syncwarp();
     }

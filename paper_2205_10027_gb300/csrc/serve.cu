@@ -82,8 +82,22 @@ int solve_batch(Engine& main, const glasso_problem* probs, int32_t count, glasso
 }
 
 // ------------------------------------------------------------------------------------------
+namespace {
+// How many admissions may go past a queue head that does not fit, per slot, before the slots
+// stop admitting anything else and give their workspaces back until it fits.
+constexpr int kSkipsPerSlot = 4;
+}  // namespace
+
 Server::Server(const glasso_config& cfg) : cfg_(cfg) {
   const int slots = std::max(1, cfg.serve_slots);
+  budget_ = cfg.hbm_budget_bytes;
+  if (!budget_) {
+    // no budget: residents may hold a quarter of the memory free at start
+    size_t fr = 0, tot = 0;
+    CUDA_CHECK(cudaSetDevice(cfg.device));
+    CUDA_CHECK(cudaMemGetInfo(&fr, &tot));
+    resident_cap_ = fr / 4;
+  }
   slot_bytes_.assign(slots, 0);
   for (int s = 0; s < slots; ++s) threads_.emplace_back([this, s] { worker(s); });
 }
@@ -95,12 +109,22 @@ Server::~Server() {
   }
   cv_.notify_all();
   for (auto& t : threads_) t.join();
+  cudaSetDevice(cfg_.device);
+  cudaDeviceSynchronize();
+  for (auto& d : cache_)
+    for (auto& e : d.second) cudaFree(e.second.mem);
+  for (double* p : to_free_) cudaFree(p);
 }
 
 int Server::submit(const glasso_request& req, uint64_t* ticket) {
   const int np = (int)round_up(req.n, kPad);
-  if (cfg_.hbm_budget_bytes && Workspace::bytes_for(np) > cfg_.hbm_budget_bytes)
+  if (budget_ && Workspace::bytes_for(np) > budget_)
     throw Error(GLASSO_ERR_BUDGET, "request can never fit the HBM budget");
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (started_ == (int)slot_bytes_.size() && alive_ == 0)
+      throw Error(dead_status_ ? dead_status_ : GLASSO_ERR_CUDA, "no serving slot is running: " + dead_msg_);
+  }
   Request r;
   r.n = req.n;
   r.S.resize((size_t)req.n * req.n);
@@ -119,6 +143,7 @@ int Server::submit(const glasso_request& req, uint64_t* ticket) {
     r.id = next_id_++;
     *ticket = r.id;
     queue_.push_back(std::move(r));
+    if (started_ == (int)slot_bytes_.size() && alive_ == 0) fail_all_queued(dead_status_, dead_msg_);
   }
   cv_.notify_all();
   return GLASSO_OK;
@@ -134,10 +159,100 @@ int Server::poll(uint64_t ticket, glasso_result* res, double* theta_out) {
     throw Error(GLASSO_ERR_ARG, "unknown ticket");
   }
   if (res) *res = it->second.res;
-  if (theta_out) std::memcpy(theta_out, it->second.theta.data(), sizeof(double) * it->second.theta.size());
+  if (theta_out && !it->second.theta.empty())
+    std::memcpy(theta_out, it->second.theta.data(), sizeof(double) * it->second.theta.size());
   const int st = it->second.res.status;
   done_.erase(it);
   return st;
+}
+
+void Server::fail_all_queued(int status, const std::string& msg) {
+  (void)msg;
+  for (auto& q : queue_) {
+    Finished f;
+    std::memset(&f.res, 0, sizeof(f.res));
+    f.res.status = status ? status : GLASSO_ERR_CUDA;
+    f.res.t_submit = q.t_submit;
+    done_[q.id] = std::move(f);
+  }
+  queue_.clear();
+}
+
+bool Server::evict_for(size_t need) {
+  // residents fit when workspaces + residents + need stay within the budget (or, with no
+  // budget, residents + need within the resident cap)
+  auto over = [&]() {
+    return budget_ ? in_use_ + resident_bytes_ + need > budget_ : resident_bytes_ + need > resident_cap_;
+  };
+  while (over()) {
+    std::map<double, Resident>* best_map = nullptr;
+    std::map<double, Resident>::iterator best;
+    uint64_t oldest = UINT64_MAX;
+    for (auto& d : cache_)
+      for (auto it = d.second.begin(); it != d.second.end(); ++it)
+        if (it->second.readers == 0 && it->second.last_use < oldest) {
+          oldest = it->second.last_use;
+          best_map = &d.second;
+          best = it;
+        }
+    if (!best_map) return false;
+    resident_bytes_ -= best->second.bytes();
+    to_free_.push_back(best->second.mem);  // freed once the lock is released
+    best_map->erase(best);
+  }
+  return true;
+}
+
+// Stream-ordered frees of evicted residents (no stream uses them: a reader synchronises its
+// stream before it lets go of an entry), outside the lock so no slot waits on them.
+void Server::free_evicted(std::vector<double*>& victims, cudaStream_t st) {
+  for (double* p : victims) cudaFreeAsync(p, st);
+  victims.clear();
+}
+
+bool Server::admit(int slot, Request& out, bool& shrink) {
+  if (queue_.empty()) return false;
+  const size_t mine = slot_bytes_[slot];
+  const size_t others = in_use_ - mine;
+  size_t evictable = 0;
+  for (auto& d : cache_)
+    for (auto& e : d.second)
+      if (e.second.readers == 0) evictable += e.second.bytes();
+  // 1: fits keeping this slot's workspace, 2: fits once the slot shrinks it to the request's
+  auto fit = [&](size_t need) -> int {
+    if (!budget_) return 1;
+    const size_t floor = resident_bytes_ - evictable;  // residents that cannot be evicted now
+    if (others + std::max(need, mine) + floor <= budget_) return 1;
+    if (others + need + floor <= budget_) return 2;
+    return 0;
+  };
+  auto take = [&](std::deque<Request>::iterator it, int how) {
+    const size_t need = Workspace::bytes_for((int)round_up(it->n, kPad));
+    const size_t ws = how == 1 ? std::max(need, mine) : need;
+    in_use_ = others + ws;
+    slot_bytes_[slot] = ws;
+    shrink = how == 2 && mine > 0;
+    evict_for(0);  // residents give way to the admitted workspace
+    out = std::move(*it);
+    queue_.erase(it);
+  };
+  auto head = queue_.begin();
+  const int h = fit(Workspace::bytes_for((int)round_up(head->n, kPad)));
+  if (h) {
+    take(head, h);
+    return true;
+  }
+  // the head does not fit now: later requests may go first a bounded number of times
+  if (head->skipped >= kSkipsPerSlot * (int)slot_bytes_.size()) return false;
+  for (auto it = std::next(head); it != queue_.end(); ++it) {
+    const int f = fit(Workspace::bytes_for((int)round_up(it->n, kPad)));
+    if (f) {
+      ++head->skipped;
+      take(it, f);
+      return true;
+    }
+  }
+  return false;
 }
 
 void Server::worker(int slot) {
@@ -145,66 +260,162 @@ void Server::worker(int slot) {
   glasso_config c = cfg_;
   c.stream = nullptr;
   std::unique_ptr<Engine> eng;
+  int fail_status = 0;
+  std::string fail_msg;
   try {
+    // GLASSO_TEST_FAIL_SLOTS=k: the first k slots report an allocation failure instead of
+    // building their engine (host-side failure injection for the tests of this path)
+    const char* tf = std::getenv("GLASSO_TEST_FAIL_SLOTS");
+    if (tf && slot < std::atoi(tf)) throw Error(GLASSO_ERR_OOM, "slot engine allocation failed (injected)");
     eng = std::make_unique<Engine>(c);
-  } catch (...) {
-    return;
+  } catch (const Error& e) {
+    fail_status = e.status;
+    fail_msg = e.what();
+  } catch (const std::exception& e) {
+    fail_status = GLASSO_ERR_CUDA;
+    fail_msg = e.what();
   }
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++started_;
+    if (eng) {
+      ++alive_;
+    } else if (!dead_status_) {
+      dead_status_ = fail_status;
+      dead_msg_ = fail_msg;
+    }
+    if (started_ == (int)slot_bytes_.size() && alive_ == 0) fail_all_queued(dead_status_, dead_msg_);
+  }
+  cv_.notify_all();
+  if (!eng) return;
+  std::vector<double*> victims;
   for (;;) {
     Request r;
-    std::shared_ptr<const std::vector<double>> warm;
+    bool shrink = false;
+    Resident* warm = nullptr;
+    Engine::Resident wr;
     {
       std::unique_lock<std::mutex> lk(mu_);
-      cv_.wait(lk, [&] {
-        if (stop_) return true;
-        if (queue_.empty()) return false;
-        const size_t need = Workspace::bytes_for((int)round_up(queue_.front().n, kPad));
-        const size_t mine = std::max(need, slot_bytes_[slot]);
-        return !cfg_.hbm_budget_bytes || in_use_ - slot_bytes_[slot] + mine <= cfg_.hbm_budget_bytes;
-      });
-      if (stop_) return;
-      r = std::move(queue_.front());
-      queue_.pop_front();
-      const size_t need = Workspace::bytes_for((int)round_up(r.n, kPad));
-      if (need > slot_bytes_[slot]) {
-        in_use_ += need - slot_bytes_[slot];
-        slot_bytes_[slot] = need;
+      for (;;) {
+        if (stop_) return;
+        if (admit(slot, r, shrink)) {
+          victims.swap(to_free_);
+          break;
+        }
+        if (!queue_.empty() && slot_bytes_[slot] > 0) {
+          // a queued request waits and this slot is idle: give its workspace back
+          in_use_ -= slot_bytes_[slot];
+          slot_bytes_[slot] = 0;
+          lk.unlock();
+          eng->release_workspace();
+          lk.lock();
+          cv_.notify_all();
+          continue;
+        }
+        cv_.wait(lk);
       }
       running_[r.id] = slot;
       if (r.dataset >= 0) {
+        // warm start: the resident solution of the same dataset with the nearest lambda
         auto ci = cache_.find(r.dataset);
         if (ci != cache_.end() && !ci->second.empty()) {
           auto hi = ci->second.lower_bound(r.lam);
-          auto best = ci->second.end();
           double bd = INFINITY;
           for (auto cand : {hi, hi == ci->second.begin() ? ci->second.end() : std::prev(hi)}) {
-            if (cand == ci->second.end()) continue;
+            if (cand == ci->second.end() || cand->second.n != r.n) continue;
             const double d = std::fabs(cand->first - r.lam);
-            if (d < bd) { bd = d; best = cand; }
+            if (d < bd) {
+              bd = d;
+              warm = &cand->second;
+            }
           }
-          if (best != ci->second.end() && best->second->size() == r.S.size()) warm = best->second;
+          if (warm) {
+            ++warm->readers;
+            warm->last_use = ++clock_;
+            const size_t m = (size_t)warm->np * warm->np;
+            wr.n = warm->n;
+            wr.np = warm->np;
+            wr.theta = warm->mem;
+            wr.li = warm->mem + m;
+            wr.w = warm->mem + 2 * m;
+            wr.logdet = warm->logdet;
+          }
         }
       }
     }
+    free_evicted(victims, eng->stream());
+    if (shrink) eng->release_workspace();
     Finished f;
     std::memset(&f.res, 0, sizeof(f.res));
     const double t_start = monotonic_seconds();
     f.theta.resize(r.S.size());
+    bool solved = false;
     try {
-      SolveOut o = eng->solve(r.S.data(), false, false, r.n, r.lam, r.tol,
-                              warm ? warm->data() : nullptr, f.theta.data());
+      SolveOut o = warm ? eng->solve_resident(r.S.data(), false, r.n, r.lam, r.tol, wr, f.theta.data())
+                        : eng->solve(r.S.data(), false, false, r.n, r.lam, r.tol, nullptr, f.theta.data());
       to_result(&f.res, o);
+      solved = true;
     } catch (const Error& e) {
       f.res.status = e.status;
     }
     f.res.t_submit = r.t_submit;
     f.res.t_start = t_start;
     f.res.t_done = monotonic_seconds();
+    // keep the solution resident for later warm starts (same dataset id)
+    double* mem = nullptr;
+    const int np = (int)round_up(r.n, kPad);
+    const size_t rbytes = (size_t)3 * np * np * sizeof(double);
+    if (solved && f.res.status == GLASSO_OK && r.dataset >= 0) {
+      bool room;
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (warm) --warm->readers;
+        warm = nullptr;
+        room = evict_for(rbytes);
+        if (room) resident_bytes_ += rbytes;  // reserved
+        victims.swap(to_free_);
+      }
+      free_evicted(victims, eng->stream());
+      if (room) {
+        double logdet = 0.0;
+        bool ok = cudaMallocAsync((void**)&mem, rbytes, eng->stream()) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        if (ok) {
+          try {
+            const size_t m = (size_t)np * np;
+            logdet = eng->export_resident(mem, mem + m, mem + 2 * m);
+          } catch (const Error&) {
+            ok = false;
+          }
+        }
+        std::lock_guard<std::mutex> lk(mu_);
+        auto& slotmap = cache_[r.dataset];
+        auto old = slotmap.find(r.lam);
+        if (ok && (old == slotmap.end() || old->second.readers == 0)) {
+          if (old != slotmap.end()) {
+            resident_bytes_ -= old->second.bytes();
+            to_free_.push_back(old->second.mem);
+            slotmap.erase(old);
+          }
+          Resident e;
+          e.n = r.n;
+          e.np = np;
+          e.mem = mem;
+          e.logdet = logdet;
+          e.last_use = ++clock_;
+          slotmap.emplace(r.lam, e);
+        } else {
+          resident_bytes_ -= rbytes;
+          if (mem) to_free_.push_back(mem);
+        }
+        victims.swap(to_free_);
+      }
+      free_evicted(victims, eng->stream());
+    }
     {
       std::lock_guard<std::mutex> lk(mu_);
+      if (warm) --warm->readers;
       running_.erase(r.id);
-      if (r.dataset >= 0 && (f.res.status == GLASSO_OK))
-        cache_[r.dataset][r.lam] = std::make_shared<const std::vector<double>>(f.theta);
       done_[r.id] = std::move(f);
     }
     cv_.notify_all();

@@ -113,3 +113,11 @@ def test_binding_structures_follow_the_header_field_order(glasso):
         py = getattr(glasso, cname)
         # (a trailing underscore stands for a Python keyword: lambda_)
         assert _struct_fields(cname) == [f.rstrip("_") for f, _ in py._fields_], cname
+
+
+def test_workspace_bytes_needs_no_gpu(glasso):
+    sizes = [glasso.workspace_bytes(n) for n in (1, 128, 129, 1000, 10000)]
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[3] < sizes[4]   # padded to multiples of 128
+    assert sizes[4] >= 12 * 8 * 10000 ** 2                          # at least the FP64 matrices
+    v = C.c_size_t()
+    assert glasso.glasso_workspace_bytes(0, C.byref(v)) == 1

@@ -116,3 +116,71 @@ def test_served_budget_rejects_oversized(glasso):
         with pytest.raises(glasso.GlassoError) as e:
             h.submit(np.eye(300), 0.1, 1e-6)
         assert e.value.status == 6
+
+
+def test_served_budget_admits_after_high_water(glasso):
+    """Three slots each keep a workspace from a medium request; a larger request that fits the
+    budget alone, but not beside those high-water workspaces, must still be admitted (idle
+    slots give their workspaces back while a queued request waits)."""
+    mid, big = 2000, 3000
+    w_mid, w_big = glasso.workspace_bytes(mid), glasso.workspace_bytes(big)
+    budget = int(1.5 * w_big)
+    assert 3 * w_mid <= budget < 2 * w_mid + w_big   # the blocked configuration
+    Sm = inputs.sample_covariance(inputs.theta_chain(mid), mid, np.random.default_rng(11))
+    Sb = inputs.sample_covariance(inputs.theta_chain(big), big, np.random.default_rng(12))
+    with glasso.Handle(precision="bf16x3", serve_slots=3, hbm_budget_bytes=budget) as h:
+        ts = [h.submit(Sm, 0.2, 1e-5) for _ in range(3)]
+        out = _drain(h, ts, [mid] * 3)
+        assert all(o[0] == 0 for o in out)
+        t = h.submit(Sb, 0.2, 1e-5)
+        st, res, _ = _drain(h, [t], [big], timeout=120.0)[0]
+    assert st == 0 and res["iterations"] > 0
+
+
+def test_served_slot_failure_is_reported(glasso, monkeypatch):
+    """A slot whose engine cannot be built (failure injected on the host) leaves the others
+    serving; with every slot failed, queued requests end with the failure's status instead of
+    staying pending, and further submits are refused."""
+    n = 120
+    S = inputs.sample_covariance(inputs.theta_chain(n), n, np.random.default_rng(13))
+    monkeypatch.setenv("GLASSO_TEST_FAIL_SLOTS", "1")
+    with glasso.Handle(precision="fp64", serve_slots=2) as h:
+        ts = [h.submit(S, 0.2, 1e-8) for _ in range(3)]
+        assert all(o[0] == 0 for o in _drain(h, ts, [n] * 3))
+    monkeypatch.setenv("GLASSO_TEST_FAIL_SLOTS", "8")
+    with glasso.Handle(precision="fp64", serve_slots=2) as h:
+        t = h.submit(S, 0.2, 1e-8)
+        t0 = time.time()
+        while True:
+            try:
+                st = h.poll(t)[0]
+            except glasso.GlassoError as e:   # a finished request with an error status
+                st = e.status
+            if st != 11:
+                break
+            assert time.time() - t0 < 30.0, "request left pending with no slot alive"
+            time.sleep(0.01)
+        assert st == 5   # GLASSO_ERR_OOM, the injected failure
+        with pytest.raises(glasso.GlassoError) as e:
+            h.submit(S, 0.2, 1e-8)
+        assert e.value.status == 5
+
+
+def test_served_resident_warm_start(glasso):
+    """Solutions stay on the device: a request warm-started from the resident state of the
+    same dataset (its Theta, inverse factor and W) reaches the same optimum as a cold solve in
+    fewer iterations, in every form, and repeating a lambda takes no iteration."""
+    n = 300
+    S = inputs.sample_covariance(inputs.theta_grid(18, n=n), n, np.random.default_rng(14))
+    for prec in ("fp64", "bf16x3"):
+        with glasso.Handle(precision=prec, serve_slots=2) as h:
+            r1 = _drain(h, [h.submit(S, 0.2, 1e-8, dataset_id=9)], [n])[0]
+            r2 = _drain(h, [h.submit(S, 0.18, 1e-8, dataset_id=9)], [n])[0]
+            r3 = _drain(h, [h.submit(S, 0.18, 1e-8, dataset_id=9)], [n])[0]
+            cold = _drain(h, [h.submit(S, 0.18, 1e-8)], [n])[0]
+        assert r1[0] == r2[0] == r3[0] == cold[0] == 0
+        assert r2[1]["iterations"] < cold[1]["iterations"]
+        assert r3[1]["iterations"] == 0
+        assert _rel(r2[2], cold[2]) <= 1e-6
+        ref = pista.pista(S, 0.18, tol=1e-8)
+        assert _rel(r2[2], ref["theta"]) <= 1e-6

@@ -2,14 +2,17 @@
 
 Fallback step (Sec. 6; reading R5).  With t_min = 2 the halving loop never runs, so every
 iteration takes t_f = (0.9 / cond_2 Theta)^2.  The GPU estimates cond_2 = lambda_max(Theta)
-lambda_max(W) by 60 power iterations, which are accurate to about 1e-3 relative, so its t_f
-agrees with the oracle's eigenvalue-based one to about 1e-2 (t_f is the square of 1/cond);
-given the GPU's own t, everything else of the step is fixed, and the oracle replays the GPU's
-step sizes (pista(fallback=...)) to check the iterates themselves:
+lambda_max(W) by 300 power iterations; its t_f agrees with the oracle's eigenvalue-based one
+to 1e-2 (t_f is the square of 1/cond).  Given the GPU's own t, everything else of the step is
+fixed, and the oracle replays the GPU's step sizes (pista(fallback=...)) to check the
+iterates themselves:
   * first step from the diagonal start: Theta^1 = the hand-derived first iterate at the GPU's
-    t (Theta^1_ii = a_i, Theta^1_ij = -t a_i a_j ST(S_ij, lam)) to 1e-13;
-  * eight fallback steps: the oracle, replaying the GPU's t, reaches the same iterate
-    (FP64: 1e-11 relative Frobenius; split-precision: 1e-8, the accuracy of the refined W).
+    t (Theta^1_ii = a_i, Theta^1_ij = -t a_i a_j ST(S_ij, lam)) to 1e-13 of max|Theta^1| in
+    FP64, 1e-8 in the split-precision forms (their W is refined to max|I - Theta W| <= 1e-9);
+  * eight fallback steps: the oracle, replaying the GPU's t, reaches the same iterate: FP64
+    to 1e-11 relative Frobenius; split-precision forms to 1e-4 of the distance travelled
+    (once Theta fills in, the sandwich of eq. b runs as BF16x3 products, relative error
+    <= 1e-4) plus 1e-8 of |Theta|.
 
 Tier-2 objective difference (eq. t_cond_min; reading R6).  Near convergence the accept test
 cannot resolve dF from two Cholesky log-dets, and the GPU evaluates
@@ -74,7 +77,8 @@ def test_first_fallback_step(fb_handle, workload):
     t_or = pista.fallback_step(pista.initial_point(S, p.lam))
     assert abs(t_gpu / t_or - 1.0) <= 1e-2, (t_gpu, t_or)
     want = closed.first_iterate(S, p.lam, t_gpu)
-    assert np.max(np.abs(theta - want)) <= 1e-13 * np.max(np.abs(want))
+    tol = 1e-13 if prec == "fp64" else 1e-8
+    assert np.max(np.abs(theta - want)) <= tol * np.max(np.abs(want))
     assert s["step_dF"] < 0.0
 
 
@@ -96,11 +100,18 @@ def test_fallback_path_replayed_by_oracle(fb_handle, workload):
     for k, rec in enumerate(ref["trace"]):
         t_or = pista.fallback_step(rec["theta"])
         assert abs(ts[k] / t_or - 1.0) <= 1e-2, (k, ts[k], t_or)
-    assert _rel(theta, ref["theta"]) <= (1e-11 if prec == "fp64" else 1e-8)
-    # the decreases the accept test saw agree with the oracle's
+    if prec == "fp64":
+        assert _rel(theta, ref["theta"]) <= 1e-11
+    else:
+        travelled = np.linalg.norm(ref["theta"] - pista.initial_point(S, p.lam))
+        assert np.linalg.norm(theta - ref["theta"]) <= 1e-4 * travelled + 1e-8 * np.linalg.norm(ref["theta"])
+    # the decreases the accept test saw agree with the oracle's, within the rounding band of
+    # the form (delta of reading R6 with u = 2^-53, or 2^-21 for the split-precision factor)
+    band = 1e3 * (1.0 if prec == "fp64" else 2.0 ** 32)
+    rel = 1e-6 if prec == "fp64" else 1e-3
     for k, rec in enumerate(ref["trace"]):
         assert steps[k]["step_dF"] < 0.0
-        assert abs(steps[k]["step_dF"] - rec["dF"]) <= 1e-6 * abs(rec["dF"]) + 1e3 * rec["delta"]
+        assert abs(steps[k]["step_dF"] - rec["dF"]) <= rel * abs(rec["dF"]) + band * rec["delta"]
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)

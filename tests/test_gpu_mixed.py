@@ -127,3 +127,47 @@ def test_solve_with_sparse_sandwich_matches_fp64_oracle(glasso, prec):
     r = np.sum(np.abs(pista.min_norm_subgradient(theta, g, p.lam))) / np.sum(np.abs(theta))
     assert r <= 1.05 * tol
     assert _rel(theta, ref["theta"]) <= 1e3 * tol
+
+
+@pytest.mark.parametrize("prec,margin", [("fp64", 1e-6), ("tf32x3", 1e-3), ("bf16x3", 1e-2)])
+def test_pd_decision_near_singular(glasso, prec, margin):
+    """Eq. t_cond_pd near the boundary: A = Q diag(ev) Q^T with its smallest eigenvalue +margin
+    or -margin (|A| = 2, n = 700, so the tensor-core trailing updates take part).  The factor's
+    PD flag must match the sign whenever the margin exceeds the perturbation the form's products
+    can put on the Schur complement (FP64: rounding; TF32x3: ~2^-22 |A| per entry; BF16x3:
+    ~2^-17 |A| per entry, about 1e-3 in norm at this n), and the log det of the PD case must be
+    the exact sum of log eigenvalues within the same relative perturbation."""
+    n = 700
+    rng = np.random.default_rng(71)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    ev = np.linspace(1.0, 2.0, n)
+    with glasso.Handle(precision=prec, products="dense") as h:
+        for sign in (1.0, -1.0):
+            e = ev.copy()
+            e[0] = sign * margin
+            A = (Q * e) @ Q.T
+            A = 0.5 * (A + A.T)
+            L, pd, ld = h.op_cholesky(_dev(A))
+            assert pd == (sign > 0), (prec, sign)
+            if pd:
+                want = float(np.sum(np.log(e)))
+                assert abs(ld - want) <= {"fp64": 1e-9, "tf32x3": 1e-3, "bf16x3": 5e-2}[prec] * abs(want)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_fp64_and_fp32_panels_agree(glasso, prec):
+    """The FP64-panel factorisation (the default) and the FP32-panel option factor the same
+    matrix to within the split products' error, and the FP64 panels' log det is the closer
+    one to the FP64 oracle's at this size."""
+    n = 1300
+    A, _ = _iterate_like(n, 77)
+    _, ldref = pista.logdet(A)
+    out = {}
+    for fp32 in (False, True):
+        with glasso.Handle(precision=prec, products="dense", fp32_panels=fp32) as h:
+            L, pd, ld = h.op_cholesky(_dev(A))
+        assert pd
+        out[fp32] = (L.cpu().numpy(), ld)
+    assert _rel(out[False][0], out[True][0]) <= TOL[prec]["chol"]
+    assert abs(out[False][1] - ldref) <= TOL[prec]["logdet"] * abs(ldref)
+    assert abs(out[True][1] - ldref) <= TOL[prec]["logdet"] * abs(ldref)
