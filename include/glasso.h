@@ -102,6 +102,15 @@ typedef struct {
                                only feeds split-precision products, is formed in FP32.
                                1: 128 x 128 panels factored and inverted in FP32 (faster,
                                FP32-grade pivots). */
+  int autotune;             /* split-precision modes.  1 (default): the first solve of a size
+                               measures, for each dense product shape it will issue, the FP32
+                               CUDA-core kernel and the tensor-core kernel with 128 x 256 and
+                               128 x 128 tiles, and runs each shape on the fastest from then
+                               on; results are kept per GPU model in the file named by the
+                               environment variable GLASSO_TUNE_CACHE (default
+                               $HOME/.cache/glasso_gemm_tune.txt; "off": in memory only).
+                               0: the built-in rule (FP32 CUDA cores up to 256, else 128 x 256
+                               tensor-core tiles). */
 } glasso_config;
 
 typedef struct {

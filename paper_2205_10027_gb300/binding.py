@@ -33,7 +33,8 @@ class glasso_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("precision", C.c_int),
                 ("max_iter", C.c_int), ("shrink", C.c_double), ("t_min", C.c_double),
                 ("hbm_budget_bytes", C.c_size_t), ("serve_slots", C.c_int), ("products", C.c_int),
-                ("method", C.c_int), ("standardize", C.c_int), ("fp32_panels", C.c_int)]
+                ("method", C.c_int), ("standardize", C.c_int), ("fp32_panels", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class glasso_result(C.Structure):
@@ -151,11 +152,12 @@ class Handle:
     products are formed, 'auto', 'dense' or 'sparse' (glasso_products); method: 'pista'
     (Algorithm 1) or 'gista' (plain proximal gradient, glasso_method); standardize: solve on the
     correlation matrix of S (glasso_config.standardize); fp32_panels: factor the Cholesky panels
-    of the split-precision forms in FP32 instead of FP64 (glasso_config.fp32_panels)."""
+    of the split-precision forms in FP32 instead of FP64 (glasso_config.fp32_panels); autotune:
+    measure the product kernels per shape (glasso_config.autotune)."""
 
     def __init__(self, precision="fp64", device=0, stream=None, max_iter=500, shrink=0.5, t_min=1e-4,
                  hbm_budget_bytes=0, serve_slots=8, products="auto", method="pista", standardize=False,
-                 fp32_panels=False):
+                 fp32_panels=False, autotune=True):
         cfg = glasso_config()
         glasso_config_default(C.byref(cfg))
         cfg.device = device
@@ -170,6 +172,7 @@ class Handle:
         cfg.method = METHODS[method]
         cfg.standardize = 1 if standardize else 0
         cfg.fp32_panels = 1 if fp32_panels else 0
+        cfg.autotune = 1 if autotune else 0
         h = C.c_void_p()
         st = glasso_create(C.byref(cfg), C.byref(h))
         if st != OK:

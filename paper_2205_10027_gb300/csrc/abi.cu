@@ -77,6 +77,7 @@ glasso_status glasso_config_default(glasso_config* cfg) {
   cfg->method = GLASSO_METHOD_PISTA;
   cfg->standardize = 0;
   cfg->fp32_panels = 0;
+  cfg->autotune = 1;
   return GLASSO_OK;
 }
 

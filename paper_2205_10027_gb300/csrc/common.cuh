@@ -23,7 +23,7 @@ struct Scalars {
   double trsa_t, l1_t, nnz_t;          // trial pass: tr(S At), ||At||_1, nnz(At)
   double logdet_t;                     // Cholesky of the trial point
   int32_t pd_t;                        // 1 while the trial factorisation has met no bad pivot
-  int32_t pad0;
+  int32_t tc_err;                      // host mirror only: the tensor-core error word
   double tr_e, tr_e2;                  // second-order log-det difference (tier 2)
   double trsa, l1;                     // objective pieces of a given matrix
   double aux[8];

@@ -5,6 +5,7 @@
 #include <cstring>
 #include "engine.h"
 #include "gemm_tc.h"
+#include "tune.h"
 
 namespace glasso {
 
@@ -125,7 +126,7 @@ size_t Workspace::bytes_for(int np) {
   const size_t csr = (size_t)(np + 1) * 8 + (size_t)np * 4 + (size_t)csr_cap(np) * 12;
   // 11 FP64 matrices, the int8 code, the tensor-core operand splits, the CSR, and the staging
   // buffer of a host input (up to np^2 FP64)
-  return 12 * m * sizeof(double) + m + tc_scratch_bytes_for(np) + csr;
+  return 12 * m * sizeof(double) + m + 2 * tc_scratch_bytes_for(np) + csr;
 }
 
 void Workspace::release() {
@@ -140,6 +141,9 @@ void Workspace::release() {
   if (tc_scratch) cudaFree(tc_scratch);
   tc_scratch = nullptr;
   tc_scratch_bytes = 0;
+  if (tc_scratch2) cudaFree(tc_scratch2);
+  tc_scratch2 = nullptr;
+  tc_scratch2_bytes = 0;
   if (hs) cudaFreeHost(hs);
   hs = nullptr;
   cap_np = 0;
@@ -181,6 +185,8 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
     alloc(csr.val, (size_t)csr.cap * 8);
     tc_scratch_bytes = tc_scratch_bytes_for(np_new);
     if (tc_scratch_bytes) alloc(tc_scratch, tc_scratch_bytes);
+    tc_scratch2_bytes = tc_scratch_bytes;
+    if (tc_scratch2_bytes) alloc(tc_scratch2, tc_scratch2_bytes);
     if (cudaMallocHost((void**)&hs, sizeof(Scalars)) != cudaSuccess) {
       cudaGetLastError();
       hs = nullptr;
@@ -279,6 +285,11 @@ int prof_class(GemmRole r) {
 // ------------------------------------------------------------------------------------------
 Engine::Engine(const glasso_config& cfg) : cfg_(cfg) {
   CUDA_CHECK(cudaSetDevice(cfg.device));
+  {
+    cudaDeviceProp prop;
+    CUDA_CHECK(cudaGetDeviceProperties(&prop, cfg.device));
+    gpu_name_ = prop.name;
+  }
   // GLASSO_NO_GRAPHS=1 runs every factorisation launch by launch (for per-kernel profiling)
   const char* ng = std::getenv("GLASSO_NO_GRAPHS");
   use_graphs_ = !(ng && ng[0] == '1');
@@ -302,6 +313,10 @@ Engine::~Engine() {
   if (stream_) cudaStreamSynchronize(stream_);
   drop_graphs();
   if (cap_stream_) cudaStreamDestroy(cap_stream_);
+  if (wait_ev_) cudaEventDestroy(wait_ev_);
+  if (side_.st) cudaStreamDestroy(side_.st);
+  if (side_.fork) cudaEventDestroy(side_.fork);
+  if (side_.join) cudaEventDestroy(side_.join);
   ws.release();
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
 }
@@ -310,11 +325,18 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
   Profiler::Rec rec;
   prof.begin_rec(prof_class(role), gemm_flops(a, ws.np, ws.n), st, rec);
   const bool mixed = cfg_.precision != GLASSO_FP64;
-  if (mixed && gemm_f32_supported(a)) {
+  const GemmChoice ch =
+      mixed && cfg_.autotune ? tuned_choice(gpu_name_, GemmShape::of(a, cfg_.precision)) : GemmChoice::Default;
+  if (mixed && gemm_f32_supported(a) && (ch == GemmChoice::Default || ch == GemmChoice::F32)) {
     gemm_f32(a, st);
   } else if (mixed && tc_gemm_supported(a)) {
+    // products on the factorisation's side stream split their operands into a scratch of
+    // their own (they run beside products on the main stream)
+    const bool on_side = side_.st && st == side_.st;
+    const TcTile tile = ch == GemmChoice::TcSquare ? TcTile::Square : ch == GemmChoice::TcWide ? TcTile::Wide
+                                                                                               : TcTile::Default;
     tc_gemm(a, cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3,
-            ws.tc_scratch, ws.tc_scratch_bytes, st);
+            on_side ? ws.tc_scratch2 : ws.tc_scratch, on_side ? ws.tc_scratch2_bytes : ws.tc_scratch_bytes, st, tile);
   } else {
     // the FP64 kernel reads its operands tile by tile while writing C: no aliasing allowed
     if (a.C == a.A || a.C == a.B) throw Error(GLASSO_ERR_ARG, "in-place product on the FP64 kernel");
@@ -323,14 +345,104 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
   prof.end_rec(rec, st);
 }
 
+void Engine::autotune() {
+  if (cfg_.precision == GLASSO_FP64 || !cfg_.autotune || tuned_epoch_ == ws.epoch) return;
+  tuned_epoch_ = ws.epoch;
+  const int np = ws.np;
+  std::vector<GemmArgs> shapes;
+  const LeafKind kind = cfg_.fp32_panels ? LeafKind::F32 : LeafKind::F64Chol;
+  factorisation_products(np, true, kind, shapes);
+  {
+    // the step's own products: W = X^T X and the refinement W R (lower), the dense sandwich
+    // (dummy pointers: only their equality, which marks shared or in-place operands, counts)
+    const double* P = reinterpret_cast<const double*>(16);
+    const double* Q = reinterpret_cast<const double*>(32);
+    double* C = reinterpret_cast<double*>(48);
+    GemmArgs w = gemm_args(P, np, 1, P, np, 0, C, np, np, np, np, 1.0, 0.0);
+    w.lower = 1;
+    w.krule = KR_LO_ROW;
+    shapes.push_back(w);
+    GemmArgs r = gemm_args(P, np, 0, Q, np, 0, C, np, np, np, np, 1.0, 0.0);
+    r.lower = 1;
+    shapes.push_back(r);
+    GemmArgs d = gemm_args(P, np, 0, Q, np, 0, C, np, np, np, np, 1.0, 0.0);
+    shapes.push_back(d);
+  }
+  cudaStream_t st = stream_;
+  const size_t mat = sizeof(double) * ws.ld * ws.np;
+  CUDA_CHECK(cudaMemsetAsync(ws.Y, 0, mat, st));
+  CUDA_CHECK(cudaMemsetAsync(ws.T, 0, mat, st));
+  CUDA_CHECK(cudaMemsetAsync(ws.X, 0, mat, st));
+  cudaEvent_t e0, e1;
+  CUDA_CHECK(cudaEventCreate(&e0));
+  CUDA_CHECK(cudaEventCreate(&e1));
+  const TcKind tk = cfg_.precision == GLASSO_MIXED_BF16X3 ? TcKind::BF16x3 : TcKind::TF32x3;
+  std::vector<GemmShape> done;
+  for (const GemmArgs& proto : shapes) {
+    const GemmShape key = GemmShape::of(proto, cfg_.precision);
+    if (tuned(gpu_name_, key)) continue;
+    bool seen = false;
+    for (const auto& d : done) seen = seen || (!(d < key) && !(key < d));
+    if (seen) continue;
+    done.push_back(key);
+    // scratch operands with the prototype's aliasing: A in Y, B in T, C in X (or A / B)
+    GemmArgs a = proto;
+    a.A = ws.Y;
+    a.B = (proto.B == proto.A) ? ws.Y : ws.T;
+    a.C = (proto.C == proto.A) ? ws.Y : (proto.C == proto.B && proto.B != proto.A) ? ws.T : ws.X;
+    a.lda = a.ldb = a.ldc = ws.ld;
+    a.flag = nullptr;
+    double ms[4] = {0, INFINITY, INFINITY, INFINITY};
+    for (int cand = 1; cand <= 3; ++cand) {
+      if (cand == 1 && !gemm_f32_supported(a)) continue;
+      if (cand > 1 && !tc_gemm_supported(a)) continue;
+      auto run = [&] {
+        if (cand == 1) gemm_f32(a, st);
+        else tc_gemm(a, tk, ws.tc_scratch, ws.tc_scratch_bytes, st, cand == 2 ? TcTile::Wide : TcTile::Square);
+      };
+      run();  // warm
+      CUDA_CHECK(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) run();
+      CUDA_CHECK(cudaEventRecord(e1, st));
+      CUDA_CHECK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CUDA_CHECK(cudaEventElapsedTime(&t, e0, e1));
+      ms[cand] = t / 3.0;
+    }
+    int best = 0;
+    for (int cand = 1; cand <= 3; ++cand)
+      if (ms[cand] < INFINITY && (best == 0 || ms[cand] < ms[best])) best = cand;
+    if (best) record_choice(gpu_name_, key, (GemmChoice)best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 GemmFn Engine::gemm_fn() {
   return [this](const GemmArgs& a, GemmRole r, cudaStream_t st) { gemm(a, r, st); };
 }
 
+// Wait for the work queued on st: cudaStreamSynchronize, or, for engines that share the host
+// cores with many others (the slots of glasso_solve_batch and of the serving loop), a
+// blocking-sync event, so that the waiting thread sleeps instead of spinning on a core.
+cudaError_t Engine::wait_stream(cudaStream_t st) {
+  if (!blocking_sync_) return cudaStreamSynchronize(st);
+  if (!wait_ev_) {
+    const cudaError_t e = cudaEventCreateWithFlags(&wait_ev_, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t e = cudaEventRecord(wait_ev_, st);
+  if (e != cudaSuccess) return e;
+  return cudaEventSynchronize(wait_ev_);
+}
+
 void Engine::sync_scalars() {
   CUDA_CHECK(cudaMemcpyAsync(ws.hs, ws.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream_));
-  CUDA_CHECK(cudaStreamSynchronize(stream_));
-  if (cfg_.precision != GLASSO_FP64 && tc_error_flag(stream_))
+  // the tensor-core error word rides on the same wait
+  const int* err = cfg_.precision != GLASSO_FP64 ? tc_error_word() : nullptr;
+  if (err) CUDA_CHECK(cudaMemcpyAsync(&ws.hs->tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  CUDA_CHECK(wait_stream(stream_));
+  if (err && ws.hs->tc_err)
     throw Error(GLASSO_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting on its pipeline");
 }
 
@@ -363,7 +475,7 @@ void Engine::load_matrix(const void* src, bool f32, bool on_device, int64_t n, d
     int bad = 0;
     CUDA_CHECK(cudaMemcpyAsync(vm, ws.vmax, sizeof(vm), cudaMemcpyDeviceToHost, stream_));
     CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, stream_));
-    CUDA_CHECK(cudaStreamSynchronize(stream_));
+    CUDA_CHECK(wait_stream(stream_));
     if (bad) throw Error(GLASSO_ERR_NONFINITE, "S holds non-finite entries or a negative diagonal");
     if (vm[0] > 1e-12 * vm[1])
       throw Error(GLASSO_ERR_NOT_SYMMETRIC, "S is not symmetric: max |S_ij - S_ji| = " +
@@ -378,8 +490,14 @@ void Engine::factor_direct(double* L, double* Li, cudaStream_t st) {
   LAUNCH_CHECK();
   const bool split = cfg_.precision != GLASSO_FP64;
   const LeafKind kind = !split ? LeafKind::F64 : cfg_.fp32_panels ? LeafKind::F32 : LeafKind::F64Chol;
+  if (split && !side_.st) {
+    CUDA_CHECK(cudaStreamCreateWithFlags(&side_.st, cudaStreamNonBlocking));
+    CUDA_CHECK(cudaEventCreateWithFlags(&side_.fork, cudaEventDisableTiming));
+    CUDA_CHECK(cudaEventCreateWithFlags(&side_.join, cudaEventDisableTiming));
+  }
+  // profiling keeps the products in stream order (their events are recorded on one stream)
   cholesky_inverse(L, Li, ws.ld, ws.np, ws.T, ws.ld_parts, ws.pd, &ws.sc->logdet_t, gemm_fn(), st, split, kind,
-                   panel_);
+                   panel_, split && !prof.on ? &side_ : nullptr);
   CUDA_CHECK(cudaMemcpyAsync(&ws.sc->pd_t, ws.pd, sizeof(int), cudaMemcpyDeviceToDevice, st));
 }
 
@@ -497,7 +615,7 @@ void Engine::refine_inverse(cudaStream_t st) {
     }
     double h = 0.0;
     CUDA_CHECK(cudaMemcpyAsync(&h, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    CUDA_CHECK(wait_stream(st));
     ws.hs->aux[1 + sweep] = h;
     if (h < 1e-9) break;
     GemmArgs g = gemm_args(ws.W, ld, 0, ws.T, ld, 0, ws.Y, ld, np, np, np, 1.0, 0.0);
@@ -518,7 +636,7 @@ bool Engine::ensure_csr_of_A(cudaStream_t st) {
   csr_rowptr(ws.A, nullptr, ws.ld, ws.n, ws.np, ws.counts, ws.csr.rowptr, st);
   int64_t nnz = 0;
   CUDA_CHECK(cudaMemcpyAsync(&nnz, ws.csr.rowptr + ws.np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   if (nnz > ws.csr.cap) return false;
   csr_fill(ws.A, nullptr, ws.ld, ws.n, ws.np, ws.csr, st);
   csr_valid_ = true;
@@ -585,7 +703,7 @@ double Engine::power_lambda_max(const double* M, cudaStream_t st, int iters) {
   }
   double h = 0.0;
   CUDA_CHECK(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   return h;
 }
 
@@ -618,7 +736,7 @@ double Engine::congruence_radius(cudaStream_t st) {
   }
   double h = 0.0;
   CUDA_CHECK(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   return h;
 }
 
@@ -629,6 +747,8 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
   st_.launches_begin = tl_launches;
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
+  st_.launches_begin = tl_launches;
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -642,7 +762,7 @@ void Engine::begin(const void* Sin, bool s_f32, bool s_on_device, int64_t n, dou
     CUDA_CHECK(cudaMemsetAsync(ws.bad, 0, sizeof(int), st));
     standardize(ws.S, ld, n, ws.vec, ws.bad, st);
     CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    CUDA_CHECK(wait_stream(st));
     if (bad) throw Error(GLASSO_ERR_ARG, "standardize needs every S_ii > 0");
   }
   CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ld * np, st));
@@ -875,7 +995,7 @@ SolveOut Engine::finish(double* theta_out) {
       CUDA_CHECK(cudaMemcpyAsync(theta_out, ws.T, sizeof(double) * n * n, cudaMemcpyDeviceToHost, st));
     }
   }
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   SolveOut out = std::move(st_.out);
   out.iterations = st_.k;
   out.F = st_.F;
@@ -908,6 +1028,8 @@ void Engine::begin_resident(const void* Sin, bool s_f32, int64_t n, double lam, 
   st_.launches_begin = tl_launches;
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
+  st_.launches_begin = tl_launches;
   if (r.np != ws.np) throw Error(GLASSO_ERR_ARG, "resident state of another padded size");
   csr_valid_ = false;
   cudaStream_t st = stream_;
@@ -918,7 +1040,7 @@ void Engine::begin_resident(const void* Sin, bool s_f32, int64_t n, double lam, 
     CUDA_CHECK(cudaMemsetAsync(ws.bad, 0, sizeof(int), st));
     standardize(ws.S, ws.ld, n, ws.vec, ws.bad, st);
     CUDA_CHECK(cudaMemcpyAsync(&bad, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    CUDA_CHECK(wait_stream(st));
     if (bad) throw Error(GLASSO_ERR_ARG, "standardize needs every S_ii > 0");
   }
   CUDA_CHECK(cudaMemsetAsync(ws.code, 0, (size_t)ws.ld * ws.np, st));
@@ -945,7 +1067,7 @@ double Engine::export_resident(double* theta, double* li, double* w) {
   CUDA_CHECK(cudaMemcpyAsync(theta, ws.A, mat, cudaMemcpyDeviceToDevice, st));
   CUDA_CHECK(cudaMemcpyAsync(li, ws.Li, mat, cudaMemcpyDeviceToDevice, st));
   CUDA_CHECK(cudaMemcpyAsync(w, ws.W, mat, cudaMemcpyDeviceToDevice, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   return st_.ld_A;
 }
 
@@ -963,7 +1085,7 @@ SolveOut Engine::solve_resident(const void* Sin, bool s_f32, int64_t n, double l
 
 void Engine::release_workspace() {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
-  if (stream_) CUDA_CHECK(cudaStreamSynchronize(stream_));
+  if (stream_) CUDA_CHECK(wait_stream(stream_));
   drop_graphs();
   ws.release();
   csr_valid_ = false;
@@ -977,6 +1099,7 @@ void Engine::release_workspace() {
 void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double* logdet) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -993,6 +1116,7 @@ void Engine::op_cholesky(const double* A, int64_t n, double* L, int* pd, double*
 int Engine::op_inverse(const double* A, int64_t n, double* W) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -1004,7 +1128,7 @@ int Engine::op_inverse(const double* A, int64_t n, double* W) {
   if (!ws.hs->pd_t) return 0;
   compute_inverse(ws.Li, st);
   unpad(ws.W, ws.ld, n, W, st);
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   return 1;
 }
 
@@ -1012,6 +1136,7 @@ void Engine::op_gradient(const double* S, const double* A, const double* W, int6
                          double* X, int8_t* code, double sums[4]) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -1028,6 +1153,7 @@ void Engine::op_gradient(const double* S, const double* A, const double* W, int6
 void Engine::op_sandwich(const double* A, const double* X, int64_t n, double* Y) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -1037,17 +1163,18 @@ void Engine::op_sandwich(const double* A, const double* X, int64_t n, double* Y)
   csr_rowptr(ws.A, nullptr, ws.ld, n, ws.np, ws.counts, ws.csr.rowptr, st);
   int64_t nnz = 0;
   CUDA_CHECK(cudaMemcpyAsync(&nnz, ws.csr.rowptr + ws.np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
   sandwich((double)nnz, st);
   mirror_lower(ws.Y, ws.ld, ws.np, st);
   unpad(ws.Y, ws.ld, n, Y, st);
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
 }
 
 void Engine::op_trial(const double* A, const double* Y, const int8_t* code, int64_t n, double lam,
                       double t, double* At) {
   CUDA_CHECK(cudaSetDevice(cfg_.device));
   ws.ensure(n, cfg_.hbm_budget_bytes);
+  autotune();
   csr_valid_ = false;
   w_valid_ = false;
   cudaStream_t st = stream_;
@@ -1059,7 +1186,7 @@ void Engine::op_trial(const double* A, const double* Y, const int8_t* code, int6
   trial(ws.A, ws.Y, ws.code, ws.ld, ws.S, ws.ld, n, ws.np, lam, t, ws.At, ws.Lt, ws.parts,
         &ws.sc->lin_s, st);
   unpad(ws.At, ws.ld, n, At, st);
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  CUDA_CHECK(wait_stream(st));
 }
 
 }  // namespace glasso

@@ -35,6 +35,8 @@ struct Workspace {
   size_t staging_bytes = 0;
   void* tc_scratch = nullptr;             // split operands of the tensor-core GEMMs
   size_t tc_scratch_bytes = 0;
+  void* tc_scratch2 = nullptr;            // the same for products on the side stream
+  size_t tc_scratch2_bytes = 0;
   Csr csr;                                // Theta in CSR form for the sparse sandwich
   int* counts = nullptr;                  // np per-row nonzero counts
   uint64_t epoch = 0;                     // bumped at every reallocation
@@ -146,6 +148,10 @@ class Engine {
 
   // the GEMM used for a given role in the configured precision mode
   void gemm(const GemmArgs& a, GemmRole role, cudaStream_t st);
+  // Measure the kernel choices for every product shape an np x np solve issues (split-
+  // precision forms; shapes already in the tuner's table are skipped).  Uses the workspace as
+  // scratch, so it runs before a solve loads its inputs.
+  void autotune();
   GemmFn gemm_fn();
 
   Workspace ws;
@@ -169,6 +175,15 @@ class Engine {
   double power_lambda_max(const double* M, cudaStream_t st, int iters);
   double congruence_radius(cudaStream_t st);
   void sync_scalars();
+  cudaError_t wait_stream(cudaStream_t st);
+  cudaEvent_t wait_ev_ = nullptr;
+  bool blocking_sync_ = false;
+
+ public:
+  // Waits sleep on a blocking-sync event instead of spinning (engines of many-slot pools).
+  void set_blocking_sync(bool on) { blocking_sync_ = on; }
+
+ private:
 
   // CUDA graphs of the factorisation, one per (factor buffer, inverse buffer) pair
   struct FactorGraph {
@@ -182,11 +197,14 @@ class Engine {
   bool use_graphs_ = true;
   int panel_ = 0;
   cudaStream_t cap_stream_ = nullptr;
+  SideStream side_;  // the factorisation's second stream (split-precision forms)
   void drop_graphs();
   void factor_direct(double* L, double* Li, cudaStream_t st);
   void factor_graphed(double* L, double* Li, cudaStream_t st);
 
   glasso_config cfg_;
+  std::string gpu_name_;
+  uint64_t tuned_epoch_ = 0;  // workspace epoch the autotuner last covered
   SolveState st_;
   cudaStream_t stream_ = nullptr;
   bool own_stream_ = false;

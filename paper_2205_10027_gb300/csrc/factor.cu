@@ -15,7 +15,7 @@ namespace glasso {
 
 namespace {
 constexpr int NB = kNb;        // leaf size of the FP64 form (64)
-constexpr int NB32 = 128;      // leaf size of the split-precision forms (FP32 leaves)
+constexpr int NB32 = 128;      // leaf size of the split-precision forms
 
 // Factor the NB x NB diagonal block at Ablk (leading dimension ld) in place, write the
 // inverse of its factor to the lower triangle of Xblk (leading dimension ld; the caller has
@@ -262,10 +262,33 @@ constexpr size_t leaf128_smem() {
   return 3 * (size_t)L64 * L64P * sizeof(double) + 5 * (size_t)L64 * L64P * sizeof(float);
 }
 
+// 1 / d in FP64 for a pivot d > 0: the PTX approximate reciprocal refined by two Newton-
+// Raphson steps in residual form, e = 1 - d y, y <- y + y e (each step squares the relative
+// error); ~5 FP64 operations instead of a correctly rounded divide's longer sequence, which
+// matters on the pivot chain.  Pivots outside [1e-290, 1e290] take the divide.
+__device__ __forceinline__ double pivot_reciprocal(double d) {
+  if (!(d > 1e-290 && d < 1e290)) return 1.0 / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
+// The lower triangle of a 64 x 64 block in column-major order, (i, c) packed as i | c << 8:
+// the entries of columns > j are the suffix starting at col_start(j + 1).  k_leaf128 copies
+// the list into shared memory (lanes read consecutive entries).
+constexpr int kTri64N = L64 * (L64 + 1) / 2;
+__device__ uint16_t g_tri64[kTri64N];
+__device__ __forceinline__ int col_start(int c) { return c * L64 - c * (c - 1) / 2; }
+
 // FP64 Cholesky of the 64 x 64 lower triangle in a (pitch L64P), all 256 threads.  On return a
 // holds L (lower), piv[j] = L_jj^2, and *fail != 0 on a pivot that is not finite and positive.
-// inv and tcol are 64-entry shared scratch.
-__device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, int* fail) {
+// inv and tcol are 64-entry shared scratch.  Step j: thread 0 forms the next pivot (the chain);
+// the six update warps take the entries of columns > j (minus that pivot's) as one flat list,
+// so every FP64 instruction of the update runs with all 32 lanes.
+__device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, const uint16_t* tri, int* fail) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // update warps: the six on sub-partitions 1-3 (warp w runs on w % 4); warp 0 runs the chain
   const int uw = warp == 1 ? 0 : warp == 2 ? 1 : warp == 3 ? 2 : warp == 5 ? 3 : warp == 6 ? 4 : warp == 7 ? 5 : -1;
@@ -273,7 +296,7 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, in
     const double d = a[0];
     if (!(d > 0.0) || isinf(d)) *fail = 1;
     piv[0] = d;
-    inv[0] = 1.0 / d;
+    inv[0] = pivot_reciprocal(d);
   }
   __syncthreads();
   for (int j = 0; j < L64; ++j) {
@@ -286,19 +309,27 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, in
       if (!(d > 0.0) || isinf(d)) *fail = 1;
       a[(j + 1) * L64P + j + 1] = d;
       piv[j + 1] = d;
-      inv[j + 1] = 1.0 / d;
+      inv[j + 1] = pivot_reciprocal(d);
     } else if (uw >= 0) {
-      // t_i = a_ij / d_j for the rows below, then a_ic -= t_i a_cj for c > j, i >= c, except
-      // the diagonal entry (j+1, j+1), which the chain has updated
+      // t_i = a_ij / d_j for the rows below, then a_ic -= t_i a_cj over the entries of
+      // columns > j except the first, the diagonal (j+1, j+1) that the chain has updated
       if (uw < 2) {
         const int i = j + 1 + 32 * uw + lane;
         if (i < L64) tcol[i] = a[i * L64P + j] * inv[j];
       }
       asm volatile("bar.sync 1, 192;" ::: "memory");
-      for (int c = j + 1 + uw; c < L64; c += 6) {
-        const double acj = a[c * L64P + j];
-        for (int i = c + (c == j + 1 ? 1 : 0) + lane; i < L64; i += 32)
-          a[i * L64P + c] = fma(-tcol[i], acj, a[i * L64P + c]);
+      // two entries per lane per pass, all loads issued before the FP64 operations (the
+      // entries are distinct and column j is read-only in this step)
+      const int e0 = j + 1 < L64 ? col_start(j + 1) + 1 : kTri64N;
+      for (int e = e0 + 32 * uw + lane; e < kTri64N; e += 384) {
+        const int e2 = e + 192;
+        const uint16_t p0 = tri[e], p1 = e2 < kTri64N ? tri[e2] : tri[e];
+        const int i0 = p0 & 0xff, c0 = p0 >> 8, i1 = p1 & 0xff, c1 = p1 >> 8;
+        const double t0 = tcol[i0], t1 = tcol[i1];
+        const double u0 = a[c0 * L64P + j], u1 = a[c1 * L64P + j];
+        const double v0 = a[i0 * L64P + c0], v1 = a[i1 * L64P + c1];
+        a[i0 * L64P + c0] = fma(-t0, u0, v0);
+        if (e2 < kTri64N) a[i1 * L64P + c1] = fma(-t1, u1, v1);
       }
     }
     __syncthreads();
@@ -314,22 +345,54 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, in
   __syncthreads();
 }
 
-// X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch L64P): thread c
-// (< 64) forms column c by forward substitution, x_ic = (delta_ic - sum_{k<i} l_ik x_kc) / l_ii,
-// with the column held in registers (rows above c come out 0) and four partial sums per row.
-__device__ void trinv64_f32(const float* l, float* x) {
-  const int c = threadIdx.x;
-  if (c >= L64) return;
-  float xr[L64];
+// X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch L64P), all 256
+// threads, by recursive doubling: the eight 8 x 8 diagonal blocks are inverted by forward
+// substitution (one column per thread), then blocks of width w = 8, 16, 32 are joined
+// pairwise, [[X11, 0], [X21, X22]] with X21 = -X22 (L21 X11), the two w x w products of all
+// pairs of a level formed at once.  The critical path is the 8-row substitution and three
+// levels of short products instead of 64 dependent rows.  x must be zero on entry (its upper
+// triangle is left so); tmp is 64 x 64 (pitch L64P) scratch.
+__device__ void trinv64_f32(const float* l, float* x, float* tmp) {
+  const int tid = threadIdx.x;
+  if (tid < L64) {
+    // diagonal block b = tid / 8, its column c = tid % 8: rows o + c .. o + 7
+    const int o = tid & ~7, c = tid & 7;
+    float xr[8];
 #pragma unroll
-  for (int i = 0; i < L64; ++i) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = 0; r < 8; ++r) {
+      float sacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < i; ++k) s[k & 3] = fmaf(l[i * L64P + k], xr[k], s[k & 3]);
-    xr[i] = ((i == c ? 1.f : 0.f) - ((s[0] + s[1]) + (s[2] + s[3]))) / l[i * L64P + i];
+      for (int k = 0; k < r; ++k) sacc = fmaf(l[(o + r) * L64P + o + k], xr[k], sacc);
+      xr[r] = (r < c) ? 0.f : ((r == c ? 1.f : 0.f) - sacc) / l[(o + r) * L64P + o + r];
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (r >= c) x[(o + r) * L64P + o + c] = xr[r];
   }
-#pragma unroll
-  for (int i = 0; i < L64; ++i) x[i * L64P + c] = xr[i];
+  __syncthreads();
+  for (int w = 8; w < L64; w *= 2) {
+    // pairs p: rows / columns [2 w p, 2 w p + 2 w); the w x w blocks of a pair, at offsets
+    // (o + w, o) for L21 / X21 and (o, o), (o + w, o + w) for X11, X22
+    const int outs = (L64 / (2 * w)) * w * w;   // outputs of one product over all pairs: 32 w
+    // T = L21 X11 (X11 lower: k >= j)
+    for (int e = tid; e < outs; e += LEAF128_THREADS) {
+      const int pair = e / (w * w), ij = e % (w * w), i = ij / w, j = ij % w;
+      const int o = 2 * w * pair;
+      float sacc = 0.f;
+      for (int k = j; k < w; ++k) sacc = fmaf(l[(o + w + i) * L64P + o + k], x[(o + k) * L64P + o + j], sacc);
+      tmp[(o + w + i) * L64P + o + j] = sacc;
+    }
+    __syncthreads();
+    // X21 = -X22 T (X22 lower: k <= i)
+    for (int e = tid; e < outs; e += LEAF128_THREADS) {
+      const int pair = e / (w * w), ij = e % (w * w), i = ij / w, j = ij % w;
+      const int o = 2 * w * pair;
+      float sacc = 0.f;
+      for (int k = 0; k <= i; ++k) sacc = fmaf(x[(o + w + i) * L64P + o + w + k], tmp[(o + w + k) * L64P + o + j], sacc);
+      x[(o + w + i) * L64P + o + j] = -sacc;
+    }
+    __syncthreads();
+  }
 }
 
 // acc (4 x 4 block at rows r0, columns c0) = sum_k A(i, k) B(k, j) over k < 64, A(i, k) at
@@ -369,23 +432,34 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   float* f4 = f3 + M;                                // T = L21 X11
   __shared__ double piv[2 * L64], inv[L64], tcol[L64];
   __shared__ double red[32];
+  __shared__ uint16_t tri[kTri64N];
   __shared__ int fail;
   const int tid = threadIdx.x;
+  for (int e = tid; e < kTri64N; e += LEAF128_THREADS) tri[e] = g_tri64[e];
   const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;  // 4 x 4 output block of the small products
-  for (int e = tid; e < 2 * L64 * L64; e += LEAF128_THREADS) {
-    const int i = e >> 6, c = e & 63;   // i < 128: rows of the block's left column panel
-    const double v = (c <= i) ? Ablk[(int64_t)i * ld + c] : 0.0;
-    if (i < L64) a11[i * L64P + c] = v;
-    else a21[(i - L64) * L64P + c] = v;
-  }
-  for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
-    const int i = e >> 6, c = e & 63;
-    a22[i * L64P + c] = (c <= i) ? Ablk[(int64_t)(L64 + i) * ld + L64 + c] : 0.0;
+  {
+    // every thread issues its 48 loads (16 per 64 x 64 panel) before storing any
+    constexpr int PER = L64 * L64 / LEAF128_THREADS;   // 16
+    double v11[PER], v21[PER], v22[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * LEAF128_THREADS, i = e >> 6, c = e & 63;
+      v11[u] = (c <= i) ? Ablk[(int64_t)i * ld + c] : 0.0;
+      v21[u] = Ablk[(int64_t)(L64 + i) * ld + c];
+      v22[u] = (c <= i) ? Ablk[(int64_t)(L64 + i) * ld + L64 + c] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * LEAF128_THREADS, i = e >> 6, c = e & 63;
+      a11[i * L64P + c] = v11[u];
+      a21[i * L64P + c] = v21[u];
+      a22[i * L64P + c] = v22[u];
+    }
   }
   if (tid == 0) fail = 0;
   __syncthreads();
   // ---- first panel: L11 (FP64), X11 = L11^{-1} (FP32)
-  chol64_f64(a11, piv, inv, tcol, &fail);
+  chol64_f64(a11, piv, inv, tcol, tri, &fail);
   if (fail) {
     if (tid == 0) *pd = 0;
     return;
@@ -394,10 +468,11 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
     const int i = e >> 6, c = e & 63;
     f0[i * L64P + c] = f64_to_f32(a11[i * L64P + c]);
     f2[i * L64P + c] = f64_to_f32(a21[i * L64P + c]);
+    f1[i * L64P + c] = 0.f;
+    f3[i * L64P + c] = 0.f;
   }
   __syncthreads();
-  trinv64_f32(f0, f1);
-  __syncthreads();
+  trinv64_f32(f0, f1, f4);
   // ---- L21 = A21 X11^T (FP32), kept in FP64 (a21) and FP32 (f0)
   {
     float acc[4][4];
@@ -432,7 +507,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   }
   __syncthreads();
   // ---- second panel: L22 (FP64), X22 (FP32)
-  chol64_f64(a22, piv + L64, inv, tcol, &fail);
+  chol64_f64(a22, piv + L64, inv, tcol, tri, &fail);
   if (fail) {
     if (tid == 0) *pd = 0;
     return;
@@ -442,8 +517,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
     f2[i * L64P + c] = f64_to_f32(a22[i * L64P + c]);
   }
   __syncthreads();
-  trinv64_f32(f2, f3);
-  __syncthreads();
+  trinv64_f32(f2, f3, f0);
   // ---- X21 = -X22 T (FP32)
   {
     float acc[4][4];
@@ -507,6 +581,24 @@ __global__ void k_mirror_lower(double* M, int64_t ld, int np) {
 }  // namespace
 
 namespace {
+// The column-major list of the 64 x 64 lower triangle for k_leaf128's FP64 updates, written
+// to each device once, from the host thread that first factors on it (the first
+// factorisation of an engine runs directly, never inside a stream capture).
+void tri64_tables_once() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  uint16_t t[kTri64N];
+  int e = 0;
+  for (int c = 0; c < L64; ++c)
+    for (int i = c; i < L64; ++i) t[e++] = (uint16_t)(i | (c << 8));
+  CUDA_CHECK(cudaMemcpyToSymbol(g_tri64, t, sizeof(t)));
+  done[dev] = true;
+}
+
 struct Ctx {
   bool split;      // split-precision modes: in-place panel products on the tensor cores
   LeafKind kind;   // which leaf kernel factors the diagonal blocks
@@ -520,7 +612,11 @@ struct Ctx {
   const GemmFn* gemm;
   cudaStream_t st;
   size_t smem;
+  const SideStream* side;
 };
+
+// The recursion splits a block of s rows (a multiple of the leaf) into halves of whole leaves.
+int split_point(int s, int leaf) { return ((s / leaf + 1) / 2) * leaf; }
 
 // Factor the diagonal block [o, o + s) of A in place and write X = L^{-1} there:
 //   L11 X11 from the first half; L21 = A21 X11^T; A22 -= L21 L21^T; L22 X22 from the second
@@ -543,7 +639,7 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
     LAUNCH_CHECK();
     return;
   }
-  const int s1 = ((s / c.leaf + 1) / 2) * c.leaf, s2 = s - s1;
+  const int s1 = split_point(s, c.leaf), s2 = s - s1;
   chol_inv_rec(c, o, s1);
   const int64_t ld = c.ld;
   double* A21 = c.A + (int64_t)(o + s1) * ld + o;
@@ -564,13 +660,35 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
     k_copy_block<<<std::min(s2, 1024), 256, 0, c.st>>>(c.T, A21, ld, s2, s1, c.pd);
     LAUNCH_CHECK();
   }
+  // X21 = -X22 (L21 X11).  With a side stream and in-place tensor-core products, the first
+  // factor L21 X11 is formed into X21 on the side stream right away: it needs only L21 and
+  // X11, so it overlaps the trailing update and the whole right half.
+  const bool fork = in_place && c.side && c.side->st;
+  if (fork) {
+    CUDA_CHECK(cudaEventRecord(c.side->fork, c.st));
+    CUDA_CHECK(cudaStreamWaitEvent(c.side->st, c.side->fork, 0));
+    GemmArgs d = gemm_args(A21, ld, 0, X11, ld, 0, X21, ld, s2, s1, s1, 1.0, 0.0);
+    d.krule = KR_LO_COL;
+    d.flag = c.pd;
+    (*c.gemm)(d, GemmRole::Inverse, c.side->st);
+  }
   // A22 -= L21 L21^T on the lower triangle
   GemmArgs b = gemm_args(A21, ld, 0, A21, ld, 1, A22, ld, s2, s2, s1, -1.0, 1.0);
   b.lower = 1;
   b.flag = c.pd;
   (*c.gemm)(b, GemmRole::Trailing, c.st);
   chol_inv_rec(c, o + s1, s2);
-  // X21 = -X22 (L21 X11)
+  if (fork) {
+    // join: everything the side stream holds so far (this node's product among it)
+    CUDA_CHECK(cudaEventRecord(c.side->join, c.side->st));
+    CUDA_CHECK(cudaStreamWaitEvent(c.st, c.side->join, 0));
+    // X21 := -X22 X21 in place (the tensor-core product reads split copies of its operands)
+    GemmArgs e = gemm_args(X22, ld, 0, X21, ld, 0, X21, ld, s2, s1, s2, -1.0, 0.0);
+    e.krule = KR_HI_ROW;
+    e.flag = c.pd;
+    (*c.gemm)(e, GemmRole::Inverse, c.st);
+    return;
+  }
   GemmArgs d = gemm_args(A21, ld, 0, X11, ld, 0, c.T, ld, s2, s1, s1, 1.0, 0.0);
   d.krule = KR_LO_COL;
   d.flag = c.pd;
@@ -584,7 +702,7 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
 
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
                       double* logdet, const GemmFn& gemm, cudaStream_t st, bool split, LeafKind kind,
-                      int panel) {
+                      int panel, const SideStream* side) {
   const int leaf = kind == LeafKind::F64 ? NB : NB32;
   const size_t smem = kind == LeafKind::F64Chol ? leaf128_smem()
                       : kind == LeafKind::F32   ? leaf_smem(NB32, sizeof(float))
@@ -599,8 +717,9 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
                                     (int)leaf_smem(NB, sizeof(double))));
     CUDA_CHECK(cudaFuncSetAttribute(k_leaf128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf128_smem()));
   });
+  tri64_tables_once();
   CUDA_CHECK(cudaMemsetAsync(X, 0, sizeof(double) * ld * np, st));
-  Ctx c{split, kind, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem};
+  Ctx c{split, kind, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem, panel <= 0 ? side : nullptr};
   if (panel <= 0) {
     chol_inv_rec(c, 0, np);
   } else {
@@ -631,6 +750,38 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
   }
   k_sum_parts<<<1, 32, 0, st>>>(ld_parts, np / leaf, pd, logdet);
   LAUNCH_CHECK();
+}
+
+void factorisation_products(int np, bool split, LeafKind kind, std::vector<GemmArgs>& out) {
+  const int leaf = kind == LeafKind::F64 ? NB : NB32;
+  // mirrors chol_inv_rec: the panel, trailing and two inverse products of every inner node,
+  // with the operand layout and in-place flags the recursion gives them (pointers are dummies
+  // whose equality encodes aliasing)
+  std::vector<std::pair<int, int>> stack{{0, np}};
+  const double* P = reinterpret_cast<const double*>(16);
+  const double* Q = reinterpret_cast<const double*>(32);
+  double* C = reinterpret_cast<double*>(48);
+  while (!stack.empty()) {
+    const int s = stack.back().second;
+    stack.pop_back();
+    if (s <= leaf) continue;
+    const int s1 = split_point(s, leaf), s2 = s - s1;
+    const bool in_place = split && std::max(s1, s2) > kSmallGemm;
+    GemmArgs a = gemm_args(P, np, 0, Q, np, 1, in_place ? const_cast<double*>(P) : C, np, s2, s1, s1, 1.0, 0.0);
+    a.krule = KR_HI_COL;
+    out.push_back(a);
+    GemmArgs b = gemm_args(P, np, 0, P, np, 1, C, np, s2, s2, s1, -1.0, 1.0);
+    b.lower = 1;
+    out.push_back(b);
+    GemmArgs d = gemm_args(P, np, 0, Q, np, 0, C, np, s2, s1, s1, 1.0, 0.0);
+    d.krule = KR_LO_COL;
+    out.push_back(d);
+    GemmArgs e = gemm_args(Q, np, 0, in_place ? C : P, np, 0, C, np, s2, s1, s2, -1.0, 0.0);
+    e.krule = KR_HI_ROW;
+    out.push_back(e);
+    stack.push_back({0, s1});
+    stack.push_back({0, s2});
+  }
 }
 
 void inverse_merge(const double* L, double* X, int64_t ld, int np, double* T, int panel, const GemmFn& gemm,

@@ -2,6 +2,7 @@
 #pragma once
 #include <algorithm>
 #include <functional>
+#include <vector>
 #include "gemm.h"
 
 namespace glasso {
@@ -25,9 +26,21 @@ enum class LeafKind {
   F64Chol,  // 64 x 64, Cholesky, pivots and log det in FP64, inverse of the factor in FP32
   F32       // 128 x 128, Cholesky and inverse in FP32 (an option of the split-precision forms)
 };
+// side: optional second stream (with fork / join events) on which the split-precision
+// recursion runs the first inverse product of a node, X21 := L21 X11, beside the trailing
+// update and the right half, which do not depend on it; the GEMM dispatcher must give
+// products on that stream their own scratch.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, double* ld_parts, int* pd,
                       double* logdet, const GemmFn& gemm, cudaStream_t st, bool split = false,
-                      LeafKind kind = LeafKind::F64, int panel = 0);
+                      LeafKind kind = LeafKind::F64, int panel = 0, const SideStream* side = nullptr);
+
+// The dense products the recursion issues for an np x np factorisation (shapes, structure
+// and in-place flags; the pointers only encode which operands alias), for the autotuner.
+void factorisation_products(int np, bool split, LeafKind kind, std::vector<GemmArgs>& out);
 
 // Completes X = L^{-1} from the inverses of the diagonal panel blocks left by
 // cholesky_inverse(..., panel).  T is np x np scratch.

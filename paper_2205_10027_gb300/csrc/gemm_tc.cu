@@ -463,6 +463,8 @@ bool tc_gemm_supported(const GemmArgs& a) {
   return a.M % 64 == 0 && a.N % 64 == 0 && a.K % 64 == 0 && a.M > 0 && a.N > 0 && a.K > 0;
 }
 
+const int* tc_error_word() { return g_err; }
+
 int tc_error_flag(cudaStream_t st) {
   if (!g_err) return 0;
   int h = 0;
@@ -529,17 +531,19 @@ void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_byt
 }
 }  // namespace
 
-void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes, cudaStream_t st, TcTile tile) {
   static std::once_flag once;
-  static bool square = false;
+  static bool square_default = false;
   std::call_once(once, [] {
     CUDA_CHECK(cudaMalloc(&g_err, sizeof(int)));
     CUDA_CHECK(cudaMemset(g_err, 0, sizeof(int)));
-    // GLASSO_TC_TILE=128 selects the 128 x 128 tiles (for comparison); 128 x 256 otherwise
+    // GLASSO_TC_TILE=128 makes the 128 x 128 tiles the default (for comparison); the
+    // autotuner may pick either tile per product shape
     const char* t = std::getenv("GLASSO_TC_TILE");
-    square = t && std::atoi(t) == 128;
+    square_default = t && std::atoi(t) == 128;
   });
   const bool bf16 = kind == TcKind::BF16x3;
+  const bool square = tile == TcTile::Square || (tile == TcTile::Default && square_default);
   if (square)
     tc_gemm_cfg<CfgSquare>(a, bf16, scratch, scratch_bytes, st);
   else

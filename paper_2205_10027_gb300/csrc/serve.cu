@@ -74,10 +74,13 @@ int solve_batch(Engine& main, const glasso_problem* probs, int32_t count, glasso
     glasso_config c = cfg;
     c.stream = nullptr;
     extra.push_back(std::make_unique<Engine>(c));
+    extra.back()->set_blocking_sync(slots > 1);
   }
+  main.set_blocking_sync(slots > 1);
   for (int s = 1; s < slots; ++s) th.emplace_back([&, s] { cudaSetDevice(cfg.device); run(*extra[s - 1]); });
   run(main);
   for (auto& t : th) t.join();
+  main.set_blocking_sync(false);
   return first_error.load();
 }
 
@@ -268,6 +271,7 @@ void Server::worker(int slot) {
     const char* tf = std::getenv("GLASSO_TEST_FAIL_SLOTS");
     if (tf && slot < std::atoi(tf)) throw Error(GLASSO_ERR_OOM, "slot engine allocation failed (injected)");
     eng = std::make_unique<Engine>(c);
+    eng->set_blocking_sync(slot_bytes_.size() > 1);
   } catch (const Error& e) {
     fail_status = e.status;
     fail_msg = e.what();

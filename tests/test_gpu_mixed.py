@@ -6,7 +6,8 @@ hi + lo carries 22 (TF32) or 16 (BF16) significant bits, the dropped lo*lo term 
 accumulation over K add about 2^-24 sqrt(K):
   sandwich Y = A X A        TF32x3 <= 2e-5, BF16x3 <= 1e-4
   Cholesky factor           TF32x3 <= 1e-6, BF16x3 <= 1e-5;  log det within 1e-6 |log det|
-                            (the 64 x 64 leaves run in FP32)
+                            (FP64 panels; the trailing updates carry the split products'
+                            error, which bounds both)
   W after FP64 refinement   <= 1e-9 (sweeps stop once max|I - A W| < 1e-10; the residual is
                             formed in FP64)
   whole solve at tol        KKT residual (host, FP64) <= 1.05 tol, iterations within 3 of
@@ -171,3 +172,24 @@ def test_fp64_and_fp32_panels_agree(glasso, prec):
     assert _rel(out[False][0], out[True][0]) <= TOL[prec]["chol"]
     assert abs(out[False][1] - ldref) <= TOL[prec]["logdet"] * abs(ldref)
     assert abs(out[True][1] - ldref) <= TOL[prec]["logdet"] * abs(ldref)
+
+
+def test_autotuner_records_its_choices_and_agrees(glasso, tmp_path, monkeypatch):
+    """The product autotuner measures the kernels for the shapes of a size it has not seen,
+    appends its choices to the cache file, and the tuned solve reaches the same optimum as the
+    built-in kernel rule (autotune off) within the stated tolerance."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("GLASSO_TUNE_CACHE", str(path))
+    p = inputs.grid_n10000(side=32, m=200, seed=8)
+    S = np.ascontiguousarray(p.S[:1000, :1000])   # n = 1,000: padded to 1,024, used by no other test
+    tol = 1e-7
+    with glasso.Handle(precision="tf32x3") as h:
+        th1, r1 = h.solve(S, p.lam, tol)
+    with glasso.Handle(precision="tf32x3", autotune=False) as h:
+        th2, r2 = h.solve(S, p.lam, tol)
+    assert r1["status"] == 0 and r2["status"] == 0
+    lines = path.read_text().splitlines()
+    fields = [l.split("|")[1].split() for l in lines]
+    assert any(f[0] in ("512", "1024") for f in fields), lines[:5]
+    assert all(int(f[9]) in (1, 2, 3) for f in fields)
+    assert _rel(th1, th2) <= 1e3 * tol
