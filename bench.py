@@ -254,7 +254,7 @@ def run_ours(args):
     n = p.S.shape[0]
     S_dev = torch.from_numpy(np.ascontiguousarray(p.S)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream,
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, device=local, stream=stream.cuda_stream,
                        products=args.products, method=args.method)
 
     def barrier():
@@ -289,7 +289,7 @@ def run_ours(args):
     # ---- end to end through the public API, host buffers ------------------------------------
     S_pin = torch.from_numpy(np.ascontiguousarray(p.S)).pin_memory()
     out_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    he = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream,
+    he = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, device=local, stream=stream.cuda_stream,
                         max_iter=args.steps, products=args.products, method=args.method)
     he.solve(S_pin.numpy(), p.lam, 0.0, out=out_pin.numpy())  # warm the workspace
     barrier()
@@ -303,7 +303,7 @@ def run_ours(args):
     # ---- time to tolerance (device-resident) ---------------------------------------------------
     ttt = None
     if args.time_to_tol:
-        ht = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, device=local, stream=stream.cuda_stream, max_iter=2000,
+        ht = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, device=local, stream=stream.cuda_stream, max_iter=2000,
                             products=args.products, method=args.method)
         barrier()
         t0 = time.perf_counter()
@@ -394,7 +394,7 @@ def run_op(args):
     X = 0.5 * (X + X.T)
     Ad, Xd = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
     Sd = torch.from_numpy(p.S + np.eye(n)).cuda()
-    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, products=args.products)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, products=args.products)
     fn = (lambda: h.op_sandwich(Ad, Xd)) if args.op == "sandwich" else (lambda: h.op_cholesky(Sd))
     for _ in range(args.warmup):
         fn()
@@ -431,7 +431,7 @@ def run_paper_table(args):
     tab = PAPER_TABLES[args.paper_table]
     n = tab["n"]
     seeds = args.paper_seeds
-    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, max_iter=1000)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, max_iter=1000)
     rows = []
     for kind, alpha, paper_s, paper_it in tab["rows"]:
         times, its, nnz, mcc = [], [], [], []
@@ -465,7 +465,7 @@ def run_batch(args):
     probs = inputs.batch_path_problems(count=args.batch_count, seed=3)
     for p in probs:
         p["tol"] = args.batch_tol
-    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, serve_slots=args.slots, max_iter=args.batch_max_iter)
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, serve_slots=args.slots, max_iter=args.batch_max_iter)
     warm = inputs.batch_path_problems(count=min(4, len(probs)), seed=97)
     for p in warm:
         p["tol"] = args.batch_tol
@@ -475,11 +475,27 @@ def run_batch(args):
     dt = time.perf_counter() - t0
     h.close()
     flat = [r for rs in res for r in rs]
+    # the plain FP64 form one solve at a time on a seeded sample of the same problems (every
+    # lambda of each sampled problem, cold starts in the path order of glasso_solve_batch)
+    fp64 = None
+    if args.batch_fp64_sample:
+        idx = np.linspace(0, len(probs) - 1, args.batch_fp64_sample).astype(int)
+        hf = binding.Handle(precision="fp64", serve_slots=1, max_iter=args.batch_max_iter)
+        t0 = time.perf_counter()
+        _, rf = hf.solve_batch([probs[i] for i in idx])
+        dtf = time.perf_counter() - t0
+        hf.close()
+        nf = sum(len(r) for r in rf)
+        fp64 = {"problems": len(idx), "solves": nf, "seconds": dtf, "solves_per_s": nf / dtf,
+                "converged": sum(r["status"] == 0 for rs in rf for r in rs),
+                "sample": "problems at evenly spaced indices of the same list, one slot (one solve at a time)"}
     print(json.dumps({"mode": "batch", "precision": args.precision, "problems": len(probs),
                       "solves": len(flat), "seconds": dt, "solves_per_s": len(flat) / dt,
                       "slots": args.slots, "tol": args.batch_tol, "max_iter": args.batch_max_iter,
                       "converged": sum(r["status"] == 0 for r in flat),
-                      "iterations_total": sum(r["iterations"] for r in flat)}))
+                      "iterations_total": sum(r["iterations"] for r in flat),
+                      "trials_total": sum(r["trials"] for r in flat),
+                      "fp64_one_at_a_time": fp64}))
 
 
 def run_served(args):
@@ -499,7 +515,7 @@ def run_served(args):
 
     for d in sorted(set(ids.tolist())):
         S_of(int(d))
-    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, serve_slots=args.slots,
+    h = binding.Handle(precision=args.precision, fp32_panels=args.fp32_panels, autotune=not args.no_autotune, serve_slots=args.slots,
                        hbm_budget_bytes=int(args.budget_gb * 1e9), max_iter=args.batch_max_iter)
     t_start = time.perf_counter()
     tickets = []
@@ -514,7 +530,10 @@ def run_served(args):
         for t, n in tickets:
             if t in done:
                 continue
-            st, res, _ = h.poll(t)
+            try:
+                st, res, _ = h.poll(t)
+            except binding.GlassoError as e:   # a finished request with an error status
+                st, res = e.status, {"status": e.status, "t_done": time.perf_counter(), "t_submit": 0.0}
             if st != binding.PENDING:
                 done[t] = res
                 lat.append(res["t_done"] - res["t_submit"])
@@ -551,6 +570,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "tf32x3", "bf16x3"], default="bf16x3")
     ap.add_argument("--method", choices=["pista", "gista"], default="pista",
                     help="outer method (glasso_method): Algorithm 1, or plain proximal gradient")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="split-precision forms: the built-in product kernel rule instead of the autotuner")
     ap.add_argument("--fp32-panels", action="store_true",
                     help="split-precision forms: factor the Cholesky panels in FP32 (default FP64)")
     ap.add_argument("--products", choices=["auto", "dense", "sparse"], default="auto",
@@ -573,6 +594,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--batch-max-iter", type=int, default=500)
+    ap.add_argument("--batch-fp64-sample", type=int, default=4,
+                    help="problems of the batch also solved one at a time in FP64 (0: none)")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--served", type=int, default=0, help="served stream of this many requests")
     ap.add_argument("--rate", type=float, default=200.0)

@@ -442,8 +442,11 @@ void Engine::sync_scalars() {
   const int* err = cfg_.precision != GLASSO_FP64 ? tc_error_word() : nullptr;
   if (err) CUDA_CHECK(cudaMemcpyAsync(&ws.hs->tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream_));
   CUDA_CHECK(wait_stream(stream_));
-  if (err && ws.hs->tc_err)
+  if (err && ws.hs->tc_err) {
+    tc_clear_error(stream_);  // reported once; the kernels that timed out left without writing
+    CUDA_CHECK(wait_stream(stream_));
     throw Error(GLASSO_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting on its pipeline");
+  }
 }
 
 // Copy a caller matrix (n x n, leading dim n) into dst (padded), mirroring its lower

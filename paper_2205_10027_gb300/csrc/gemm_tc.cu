@@ -55,6 +55,8 @@ struct TcArgs {
   uint32_t idesc;     // tcgen05 instruction descriptor
   const int* flag;
   int* err;
+  int no_loads;       // failure injection for the tests of the timeout path: the producer
+                      // issues no load, so the MMA warp's bounded wait runs out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   if (warp == 0 && lane == 0 && nk > 0) {
     // producer: TMA loads of the four operand tiles of each k-stage
     int issued = 0;
-    for (int i = 0; i < nk; ++i) {
+    for (int i = 0; i < (p.no_loads ? 0 : nk); ++i) {
       const int s = i % STAGES;
       const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) { *s_abort = 1; break; }
@@ -448,7 +450,8 @@ void split2(const SplitJob& a, const SplitJob& b, bool bf16, cudaStream_t st, in
   LAUNCH_CHECK();
 }
 
-int* g_err = nullptr;  // device error word of the tensor-core kernels
+int* g_err = nullptr;     // device error word of the tensor-core kernels
+bool g_no_loads = false;  // GLASSO_TEST_TC_NO_LOADS=1 (read once): see TcArgs::no_loads
 }  // namespace
 
 bool tc_available() { return encode_fn() != nullptr; }
@@ -464,6 +467,10 @@ bool tc_gemm_supported(const GemmArgs& a) {
 }
 
 const int* tc_error_word() { return g_err; }
+
+void tc_clear_error(cudaStream_t st) {
+  if (g_err) CUDA_CHECK(cudaMemsetAsync(g_err, 0, sizeof(int), st));
+}
 
 int tc_error_flag(cudaStream_t st) {
   if (!g_err) return 0;
@@ -525,6 +532,7 @@ void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_byt
   p.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   p.flag = a.flag;
   p.err = g_err;
+  p.no_loads = g_no_loads ? 1 : 0;
   dim3 grid(((a.N + TN - 1) / TN) * ((a.M + TM - 1) / TM));
   k_gemm_tc<CF><<<grid, CF::THREADS, CF::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
   LAUNCH_CHECK();
@@ -541,6 +549,8 @@ void tc_gemm(const GemmArgs& a, TcKind kind, void* scratch, size_t scratch_bytes
     // autotuner may pick either tile per product shape
     const char* t = std::getenv("GLASSO_TC_TILE");
     square_default = t && std::atoi(t) == 128;
+    const char* nl = std::getenv("GLASSO_TEST_TC_NO_LOADS");
+    g_no_loads = nl && nl[0] == '1';
   });
   const bool bf16 = kind == TcKind::BF16x3;
   const bool square = tile == TcTile::Square || (tile == TcTile::Default && square_default);

@@ -27,5 +27,7 @@ int tc_error_flag(cudaStream_t st);
 // The device word the tensor-core kernels set on such a timeout (nullptr before the first
 // tensor-core product), for callers that copy it back with other results.
 const int* tc_error_word();
+// Clear that word (after its timeout has been reported), in stream order on st.
+void tc_clear_error(cudaStream_t st);
 
 }  // namespace glasso

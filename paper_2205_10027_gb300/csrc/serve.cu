@@ -130,12 +130,24 @@ int Server::submit(const glasso_request& req, uint64_t* ticket) {
   }
   Request r;
   r.n = req.n;
-  r.S.resize((size_t)req.n * req.n);
-  if (req.dtype == GLASSO_F32) {
-    const float* s = (const float*)req.S;
-    for (size_t e = 0; e < r.S.size(); ++e) r.S[e] = (double)s[e];
-  } else {
-    std::memcpy(r.S.data(), req.S, sizeof(double) * r.S.size());
+  if (req.dataset_id >= 0) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = datasets_.find(req.dataset_id);
+    if (it != datasets_.end() && it->second->size() == (size_t)req.n * req.n) r.S = it->second;
+  }
+  if (!r.S) {
+    auto v = std::make_shared<std::vector<double>>((size_t)req.n * req.n);
+    if (req.dtype == GLASSO_F32) {
+      const float* s = (const float*)req.S;
+      for (size_t e = 0; e < v->size(); ++e) (*v)[e] = (double)s[e];
+    } else {
+      std::memcpy(v->data(), req.S, sizeof(double) * v->size());
+    }
+    r.S = v;
+    if (req.dataset_id >= 0) {
+      std::lock_guard<std::mutex> lk(mu_);
+      datasets_[req.dataset_id] = r.S;
+    }
   }
   r.lam = req.lambda;
   r.tol = req.tol;
@@ -352,11 +364,11 @@ void Server::worker(int slot) {
     Finished f;
     std::memset(&f.res, 0, sizeof(f.res));
     const double t_start = monotonic_seconds();
-    f.theta.resize(r.S.size());
+    f.theta.resize(r.S->size());
     bool solved = false;
     try {
-      SolveOut o = warm ? eng->solve_resident(r.S.data(), false, r.n, r.lam, r.tol, wr, f.theta.data())
-                        : eng->solve(r.S.data(), false, false, r.n, r.lam, r.tol, nullptr, f.theta.data());
+      SolveOut o = warm ? eng->solve_resident(r.S->data(), false, r.n, r.lam, r.tol, wr, f.theta.data())
+                        : eng->solve(r.S->data(), false, false, r.n, r.lam, r.tol, nullptr, f.theta.data());
       to_result(&f.res, o);
       solved = true;
     } catch (const Error& e) {

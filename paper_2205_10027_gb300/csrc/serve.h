@@ -32,7 +32,7 @@ class Server {
   struct Request {
     uint64_t id;
     int64_t n;
-    std::vector<double> S;  // promoted to FP64
+    std::shared_ptr<const std::vector<double>> S;  // promoted to FP64; shared per dataset id
     double lam, tol;
     int64_t dataset;
     double t_submit;
@@ -80,6 +80,9 @@ class Server {
   std::string dead_msg_;
   // dataset id -> lambda -> resident solution
   std::unordered_map<int64_t, std::map<double, Resident>> cache_;
+  // dataset id -> its S (host, FP64): requests of one id share S (glasso_request), so a
+  // stream of many requests over few datasets holds one copy per dataset
+  std::unordered_map<int64_t, std::shared_ptr<const std::vector<double>>> datasets_;
   std::vector<std::thread> threads_;
 };
 
