@@ -313,6 +313,28 @@ def run_ours(args):
                "rel_kkt_l1": rt["rel_kkt_l1"], "status": binding.STATUS[rt["status"]]}
         ht.close()
 
+    # ---- the same split-precision form with FP32 Cholesky panels (glasso_config.fp32_panels),
+    # device-resident steps timed the same way, for the cost of the FP64 panels ---------------
+    fp32p = None
+    if args.precision != "fp64" and not args.fp32_panels:
+        hp = binding.Handle(precision=args.precision, fp32_panels=True, autotune=not args.no_autotune, device=local,
+                            stream=stream.cuda_stream, products=args.products, method=args.method)
+        hp.begin(S_dev, p.lam)
+        for _ in range(args.warmup):
+            hp.step(0.0)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            hp.step(0.0)
+        p1.record(stream)
+        barrier()
+        hp.end()
+        hp.close()
+        pms = max_over_ranks(p0.elapsed_time(p1))
+        fp32p = {"iters_per_s": job_throughput(args.steps, world, pms / 1000.0), "ms_per_step": pms / args.steps,
+                 "note": "same workload and steps, Cholesky panels factored in FP32 (the option glasso_config.fp32_panels)"}
+
     # ---- the plain FP64 form on the same workload (what the split-precision form must beat) --
     fp64 = None
     if args.fp64_form and args.precision != "fp64":
@@ -375,6 +397,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "time_to_tol": ttt,
             "fp64_form": fp64,
+            "fp32_panels_form": fp32p,
         }
         print(json.dumps(line))
     if world > 1:

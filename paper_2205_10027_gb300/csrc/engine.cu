@@ -346,8 +346,10 @@ void Engine::gemm(const GemmArgs& a, GemmRole role, cudaStream_t st) {
 }
 
 void Engine::autotune() {
-  if (cfg_.precision == GLASSO_FP64 || !cfg_.autotune || tuned_epoch_ == ws.epoch) return;
-  tuned_epoch_ = ws.epoch;
+  // every padded size this engine solves at is covered before its first solve, so that a
+  // shape's kernel never changes between solves of a process (results stay reproducible)
+  if (cfg_.precision == GLASSO_FP64 || !cfg_.autotune || tuned_np_ == ws.np) return;
+  tuned_np_ = ws.np;
   const int np = ws.np;
   std::vector<GemmArgs> shapes;
   const LeafKind kind = cfg_.fp32_panels ? LeafKind::F32 : LeafKind::F64Chol;

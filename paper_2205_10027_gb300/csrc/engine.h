@@ -204,7 +204,7 @@ class Engine {
 
   glasso_config cfg_;
   std::string gpu_name_;
-  uint64_t tuned_epoch_ = 0;  // workspace epoch the autotuner last covered
+  int tuned_np_ = 0;  // padded size the autotuner last covered
   SolveState st_;
   cudaStream_t stream_ = nullptr;
   bool own_stream_ = false;

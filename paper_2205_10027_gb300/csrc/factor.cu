@@ -290,12 +290,10 @@ __device__ __forceinline__ int col_start(int c) { return c * L64 - c * (c - 1) /
 // so every FP64 instruction of the update runs with all 32 lanes.
 __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, const uint16_t* tri, int* fail) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // update warps: the six on sub-partitions 1-3 (warp w runs on w % 4); warp 0 runs the chain.
-  // While the trailing triangle is large (the first kEarly columns) the update is bound by
-  // the FP64 pipes rather than by the chain, and warp 4 (sub-partition 0) joins as a seventh.
-  constexpr int kEarly = 20;
-  const int uw6 = warp == 1 ? 0 : warp == 2 ? 1 : warp == 3 ? 2 : warp == 5 ? 3 : warp == 6 ? 4 : warp == 7 ? 5 : -1;
-  const int uw7 = warp == 4 ? 6 : uw6;
+  // update warps: the six on sub-partitions 1-3 (warp w runs on w % 4); warp 0 runs the chain
+  // (a seventh update warp on sub-partition 0 was measured: it slows the chain more than it
+  // speeds the update)
+  const int uw = warp == 1 ? 0 : warp == 2 ? 1 : warp == 3 ? 2 : warp == 5 ? 3 : warp == 6 ? 4 : warp == 7 ? 5 : -1;
   if (tid == 0) {
     const double d = a[0];
     if (!(d > 0.0) || isinf(d)) *fail = 1;
@@ -305,9 +303,6 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, co
   __syncthreads();
   for (int j = 0; j < L64; ++j) {
     if (*fail) break;
-    const bool early = j < kEarly;
-    const int uw = early ? uw7 : uw6;
-    const int nu = early ? 7 : 6;
     if (tid == 0 && j + 1 < L64) {
       // the pivot chain, one column ahead: every update of a_{j+1,j} and a_{j+1,j+1} from
       // columns < j is in place (previous steps)
@@ -324,11 +319,10 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, co
         const int i = j + 1 + 32 * uw + lane;
         if (i < L64) tcol[i] = a[i * L64P + j] * inv[j];
       }
-      if (early) asm volatile("bar.sync 1, 224;" ::: "memory");
-      else asm volatile("bar.sync 2, 192;" ::: "memory");
+      asm volatile("bar.sync 1, 192;" ::: "memory");
       // two entries per lane per pass, all loads issued before the FP64 operations (the
       // entries are distinct and column j is read-only in this step)
-      const int span = 32 * nu;
+      constexpr int span = 192;
       const int e0 = j + 1 < L64 ? col_start(j + 1) + 1 : kTri64N;
       for (int e = e0 + 32 * uw + lane; e < kTri64N; e += 2 * span) {
         const int e2 = e + span;
