@@ -153,7 +153,7 @@ CLASS_BOUND = {"factor": "tensor", "inverse": "tensor", "refine": "tensor", "san
                "trailing": "tensor", "panel": "tensor", "spmm": "fp64",
                "gradient": "hbm", "trial": "hbm", "residual": "hbm", "logdet2": "hbm", "aux": "hbm"}
 CLASS_UNIT = {"factor": "whole Cholesky-with-inverse factorisations (one CUDA graph each: k_gemm_tc, k_split, "
-                        "k_gemm_f32, k_leaf64)",
+                        "k_gemm_f32, k_leaf128 in the split-precision forms, k_leaf_chol_inv in FP64)",
               "inverse": "W = X^T X (k_gemm_tc)", "refine": "refinement product W R (k_gemm_tc)",
               "sandwich": "dense sandwich products (k_gemm_tc)", "spmm": "sparse sandwich products (k_spmm)",
               "gradient": "gradient pass (k_gradient)", "trial": "trial-point pass (k_trial)",

@@ -265,9 +265,18 @@ constexpr size_t leaf128_smem() {
 // 1 / d in FP64 for a pivot d > 0: the PTX approximate reciprocal refined by two Newton-
 // Raphson steps in residual form, e = 1 - d y, y <- y + y e (each step squares the relative
 // error); ~5 FP64 operations instead of a correctly rounded divide's longer sequence, which
-// matters on the pivot chain.  Pivots outside [1e-290, 1e290] take the divide.
+// matters on the pivot chain.
+// A pivot is usable when it is a positive finite number: tested on the bit pattern with
+// integer operations, which keeps FP64 compares (one FP64 instruction each) off the chain.
+__device__ __forceinline__ bool pivot_ok(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0 && ((b >> 52) & 0x7FF) != 0x7FF;  // sign clear, not +0, not Inf or NaN
+}
+
 __device__ __forceinline__ double pivot_reciprocal(double d) {
-  if (!(d > 1e-290 && d < 1e290)) return 1.0 / d;
+  // outside [2^-960, 2^960] (exponent field tested as an integer) take the divide
+  const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
+  if (ex < 63 || ex > 1983) return 1.0 / d;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
   double e = fma(-d, y, 1.0);
@@ -285,57 +294,100 @@ __device__ __forceinline__ int col_start(int c) { return c * L64 - c * (c - 1) /
 
 // FP64 Cholesky of the 64 x 64 lower triangle in a (pitch L64P), all 256 threads.  On return a
 // holds L (lower), piv[j] = L_jj^2, and *fail != 0 on a pivot that is not finite and positive.
-// inv and tcol are 64-entry shared scratch.  Step j: thread 0 forms the next pivot (the chain);
-// the six update warps take the entries of columns > j (minus that pivot's) as one flat list,
-// so every FP64 instruction of the update runs with all 32 lanes.
-__device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, const uint16_t* tri, int* fail) {
+// inv and tcol are 64-entry shared scratch, tri the column-major list of the triangle, fs a
+// 64 x 33 FP32 shared scratch.
+//
+// The panel is factored as four 16-column micro-panels.  Inside a micro-panel the update is
+// FP64 and right-looking, kept unscaled (a_ic -= a_ij a_cj / d_j; L is a_ij / sqrt(d_j) at the
+// end): step j, one lane of warp 0 forms the next pivot d_{j+1} = a_{j+1,j+1} - a_{j+1,j}^2 / d_j
+// (the chain) while the six warps on the other sub-partitions update the micro-panel's
+// remaining columns, all rows, as a flat list so that each FP64 instruction runs 32 lanes.  A
+// finished micro-panel's contribution to the columns right of it is one FP32 product
+// (l_ik = a_ik / d_k times a_ck, 16 terms) subtracted from the FP64 entries in FP64, the way
+// the recursion above applies its trailing updates; so every pivot is FP64 arithmetic on an
+// FP64 Schur complement, and the FP64 pipe (one warp instruction per 64 cycles per
+// sub-partition here) carries only the micro-panels' own updates.
+constexpr int kMicro = 16;
+__device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, const uint16_t* tri, float* fs,
+                           int* fail) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // update warps: the six on sub-partitions 1-3 (warp w runs on w % 4); warp 0 runs the chain
-  // (a seventh update warp on sub-partition 0 was measured: it slows the chain more than it
-  // speeds the update)
   const int uw = warp == 1 ? 0 : warp == 2 ? 1 : warp == 3 ? 2 : warp == 5 ? 3 : warp == 6 ? 4 : warp == 7 ? 5 : -1;
-  if (tid == 0) {
-    const double d = a[0];
-    if (!(d > 0.0) || isinf(d)) *fail = 1;
-    piv[0] = d;
-    inv[0] = pivot_reciprocal(d);
-  }
-  __syncthreads();
-  for (int j = 0; j < L64; ++j) {
-    if (*fail) break;
-    if (tid == 0 && j + 1 < L64) {
-      // the pivot chain, one column ahead: every update of a_{j+1,j} and a_{j+1,j+1} from
-      // columns < j is in place (previous steps)
-      const double aj = a[(j + 1) * L64P + j];
-      const double d = fma(-aj * inv[j], aj, a[(j + 1) * L64P + j + 1]);
-      if (!(d > 0.0) || isinf(d)) *fail = 1;
-      a[(j + 1) * L64P + j + 1] = d;
-      piv[j + 1] = d;
-      inv[j + 1] = pivot_reciprocal(d);
-    } else if (uw >= 0) {
-      // t_i = a_ij / d_j for the rows below, then a_ic -= t_i a_cj over the entries of
-      // columns > j except the first, the diagonal (j+1, j+1) that the chain has updated
-      if (uw < 2) {
-        const int i = j + 1 + 32 * uw + lane;
-        if (i < L64) tcol[i] = a[i * L64P + j] * inv[j];
-      }
-      asm volatile("bar.sync 1, 192;" ::: "memory");
-      // two entries per lane per pass, all loads issued before the FP64 operations (the
-      // entries are distinct and column j is read-only in this step)
-      constexpr int span = 192;
-      const int e0 = j + 1 < L64 ? col_start(j + 1) + 1 : kTri64N;
-      for (int e = e0 + 32 * uw + lane; e < kTri64N; e += 2 * span) {
-        const int e2 = e + span;
-        const uint16_t p0 = tri[e], p1 = e2 < kTri64N ? tri[e2] : tri[e];
-        const int i0 = p0 & 0xff, c0 = p0 >> 8, i1 = p1 & 0xff, c1 = p1 >> 8;
-        const double t0 = tcol[i0], t1 = tcol[i1];
-        const double u0 = a[c0 * L64P + j], u1 = a[c1 * L64P + j];
-        const double v0 = a[i0 * L64P + c0], v1 = a[i1 * L64P + c1];
-        a[i0 * L64P + c0] = fma(-t0, u0, v0);
-        if (e2 < kTri64N) a[i1 * L64P + c1] = fma(-t1, u1, v1);
-      }
+  double rinv = 0.0;  // thread 0: 1 / d of the last pivot (the chain keeps it in a register)
+  for (int c0 = 0; c0 < L64; c0 += kMicro) {
+    const int c1 = c0 + kMicro;  // the micro-panel is columns [c0, c1)
+    // its first pivot: every contribution of the columns left of it is in place
+    if (tid == 0) {
+      const double d = a[c0 * L64P + c0];
+      if (!pivot_ok(d)) *fail = 1;
+      piv[c0] = d;
+      rinv = pivot_reciprocal(d);
+      inv[c0] = rinv;
     }
     __syncthreads();
+    for (int j = c0; j < c1; ++j) {
+      if (*fail) break;
+      if (tid == 0 && j + 1 < c1) {
+        // the pivot chain, one column ahead
+        const double aj = a[(j + 1) * L64P + j];
+        const double d = fma(-aj * rinv, aj, a[(j + 1) * L64P + j + 1]);
+        if (!pivot_ok(d)) *fail = 1;
+        rinv = pivot_reciprocal(d);
+        a[(j + 1) * L64P + j + 1] = d;
+        piv[j + 1] = d;
+        inv[j + 1] = rinv;
+      } else if (uw >= 0 && j + 1 < c1) {
+        // t_i = a_ij / d_j for the rows below, then a_ic -= t_i a_cj over the micro-panel's
+        // columns > j, all rows, except the diagonal (j+1, j+1) that the chain has updated
+        if (uw < 2) {
+          const int i = j + 1 + 32 * uw + lane;
+          if (i < L64) tcol[i] = a[i * L64P + j] * inv[j];
+        }
+        asm volatile("bar.sync 1, 192;" ::: "memory");
+        // two entries per lane per pass, all loads issued before the FP64 operations (the
+        // entries are distinct and column j is read-only in this step)
+        constexpr int span = 192;
+        const int e0 = col_start(j + 1) + 1, e1 = col_start(c1);
+        for (int e = e0 + 32 * uw + lane; e < e1; e += 2 * span) {
+          const int e2 = e + span;
+          const uint16_t p0 = tri[e], p1 = e2 < e1 ? tri[e2] : tri[e];
+          const int i0 = p0 & 0xff, q0 = p0 >> 8, i1 = p1 & 0xff, q1 = p1 >> 8;
+          const double t0 = tcol[i0], t1 = tcol[i1];
+          const double u0 = a[q0 * L64P + j], u1 = a[q1 * L64P + j];
+          const double v0 = a[i0 * L64P + q0], v1 = a[i1 * L64P + q1];
+          a[i0 * L64P + q0] = fma(-t0, u0, v0);
+          if (e2 < e1) a[i1 * L64P + q1] = fma(-t1, u1, v1);
+        }
+      }
+      __syncthreads();
+    }
+    if (*fail) break;
+    if (c1 < L64) {
+      // the micro-panel's contribution to the trailing block: FP32 copies of l_ik = a_ik / d_k
+      // (fs[r][k]) and of a_ik (fs[r][16 + k]) for rows r = i - c1, then
+      // a_ic -= sum_k l_ik a_ck for c1 <= c <= i, formed in FP32, subtracted in FP64
+      const int rows = L64 - c1;
+      for (int e = tid; e < rows * kMicro; e += LEAF128_THREADS) {
+        const int r = e / kMicro, k = e % kMicro;
+        const double u = a[(c1 + r) * L64P + c0 + k];
+        fs[r * 33 + k] = f64_to_f32(u * inv[c0 + k]);
+        fs[r * 33 + kMicro + k] = f64_to_f32(u);
+      }
+      __syncthreads();
+      const int ntri = rows * (rows + 1) / 2;
+      for (int e = tid; e < ntri; e += LEAF128_THREADS) {
+        // entry e of the trailing lower triangle in row-major order: row r, column q <= r
+        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while (r * (r + 1) / 2 > e) --r;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        const int q = e - r * (r + 1) / 2;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMicro; ++k) acc = fmaf(fs[r * 33 + k], fs[q * 33 + kMicro + k], acc);
+        a[(c1 + r) * L64P + c1 + q] -= f32_to_f64(acc);
+      }
+      __syncthreads();
+    }
   }
   if (*fail) return;
   // L_ij = a_ij / sqrt(d_j) (i > j), L_jj = sqrt(d_j)
@@ -348,14 +400,41 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, co
   __syncthreads();
 }
 
+// One joining level of the recursive-doubling inverse: for every pair of W x W diagonal blocks
+// [[X11, 0], [X21, X22]] of X, X21 = -X22 (L21 X11), the two W x W products of all pairs formed
+// at once (T in tmp).
+template <int W>
+__device__ __forceinline__ void trinv_join(const float* l, float* x, float* tmp) {
+  constexpr int OUTS = (L64 / (2 * W)) * W * W;  // outputs of one product over all pairs: 32 W
+  const int tid = threadIdx.x;
+  // T = L21 X11 (X11 lower: k >= j)
+  for (int e = tid; e < OUTS; e += LEAF128_THREADS) {
+    const int pair = e / (W * W), ij = e % (W * W), i = ij / W, j = ij % W;
+    const int o = 2 * W * pair;
+    float sacc = 0.f;
+    for (int k = j; k < W; ++k) sacc = fmaf(l[(o + W + i) * L64P + o + k], x[(o + k) * L64P + o + j], sacc);
+    tmp[(o + W + i) * L64P + o + j] = sacc;
+  }
+  __syncthreads();
+  // X21 = -X22 T (X22 lower: k <= i)
+  for (int e = tid; e < OUTS; e += LEAF128_THREADS) {
+    const int pair = e / (W * W), ij = e % (W * W), i = ij / W, j = ij % W;
+    const int o = 2 * W * pair;
+    float sacc = 0.f;
+    for (int k = 0; k <= i; ++k) sacc = fmaf(x[(o + W + i) * L64P + o + W + k], tmp[(o + W + k) * L64P + o + j], sacc);
+    x[(o + W + i) * L64P + o + j] = -sacc;
+  }
+  __syncthreads();
+}
+
 // X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch L64P), all 256
 // threads, by recursive doubling: the eight 8 x 8 diagonal blocks are inverted by forward
-// substitution (one column per thread), then blocks of width w = 8, 16, 32 are joined
-// pairwise, [[X11, 0], [X21, X22]] with X21 = -X22 (L21 X11), the two w x w products of all
-// pairs of a level formed at once.  The critical path is the 8-row substitution and three
-// levels of short products instead of 64 dependent rows.  x must be zero on entry (its upper
-// triangle is left so); tmp is 64 x 64 (pitch L64P) scratch.
-__device__ void trinv64_f32(const float* l, float* x, float* tmp) {
+// substitution (one column per thread, 1 / l_ii from rdiag, the FP64 reciprocal diagonal the
+// panel left), then blocks of width 8, 16, 32 are joined pairwise (trinv_join).  The critical
+// path is the 8-row substitution and three levels of short products instead of 64 dependent
+// rows.  x must be zero on entry (its upper triangle is left so); tmp is 64 x 64 (pitch L64P)
+// scratch.
+__device__ void trinv64_f32(const float* l, const double* rdiag, float* x, float* tmp) {
   const int tid = threadIdx.x;
   if (tid < L64) {
     // diagonal block b = tid / 8, its column c = tid % 8: rows o + c .. o + 7
@@ -366,36 +445,16 @@ __device__ void trinv64_f32(const float* l, float* x, float* tmp) {
       float sacc = 0.f;
 #pragma unroll
       for (int k = 0; k < r; ++k) sacc = fmaf(l[(o + r) * L64P + o + k], xr[k], sacc);
-      xr[r] = (r < c) ? 0.f : ((r == c ? 1.f : 0.f) - sacc) / l[(o + r) * L64P + o + r];
+      xr[r] = (r < c) ? 0.f : ((r == c ? 1.f : 0.f) - sacc) * (float)rdiag[o + r];
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r)
       if (r >= c) x[(o + r) * L64P + o + c] = xr[r];
   }
   __syncthreads();
-  for (int w = 8; w < L64; w *= 2) {
-    // pairs p: rows / columns [2 w p, 2 w p + 2 w); the w x w blocks of a pair, at offsets
-    // (o + w, o) for L21 / X21 and (o, o), (o + w, o + w) for X11, X22
-    const int outs = (L64 / (2 * w)) * w * w;   // outputs of one product over all pairs: 32 w
-    // T = L21 X11 (X11 lower: k >= j)
-    for (int e = tid; e < outs; e += LEAF128_THREADS) {
-      const int pair = e / (w * w), ij = e % (w * w), i = ij / w, j = ij % w;
-      const int o = 2 * w * pair;
-      float sacc = 0.f;
-      for (int k = j; k < w; ++k) sacc = fmaf(l[(o + w + i) * L64P + o + k], x[(o + k) * L64P + o + j], sacc);
-      tmp[(o + w + i) * L64P + o + j] = sacc;
-    }
-    __syncthreads();
-    // X21 = -X22 T (X22 lower: k <= i)
-    for (int e = tid; e < outs; e += LEAF128_THREADS) {
-      const int pair = e / (w * w), ij = e % (w * w), i = ij / w, j = ij % w;
-      const int o = 2 * w * pair;
-      float sacc = 0.f;
-      for (int k = 0; k <= i; ++k) sacc = fmaf(x[(o + w + i) * L64P + o + w + k], tmp[(o + w + k) * L64P + o + j], sacc);
-      x[(o + w + i) * L64P + o + j] = -sacc;
-    }
-    __syncthreads();
-  }
+  trinv_join<8>(l, x, tmp);
+  trinv_join<16>(l, x, tmp);
+  trinv_join<32>(l, x, tmp);
 }
 
 // acc (4 x 4 block at rows r0, columns c0) = sum_k A(i, k) B(k, j) over k < 64, A(i, k) at
@@ -462,7 +521,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   if (tid == 0) fail = 0;
   __syncthreads();
   // ---- first panel: L11 (FP64), X11 = L11^{-1} (FP32)
-  chol64_f64(a11, piv, inv, tcol, tri, &fail);
+  chol64_f64(a11, piv, inv, tcol, tri, f0, &fail);
   if (fail) {
     if (tid == 0) *pd = 0;
     return;
@@ -475,7 +534,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
     f3[i * L64P + c] = 0.f;
   }
   __syncthreads();
-  trinv64_f32(f0, f1, f4);
+  trinv64_f32(f0, tcol, f1, f4);
   // ---- L21 = A21 X11^T (FP32), kept in FP64 (a21) and FP32 (f0)
   {
     float acc[4][4];
@@ -510,7 +569,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   }
   __syncthreads();
   // ---- second panel: L22 (FP64), X22 (FP32)
-  chol64_f64(a22, piv + L64, inv, tcol, tri, &fail);
+  chol64_f64(a22, piv + L64, inv, tcol, tri, f2, &fail);
   if (fail) {
     if (tid == 0) *pd = 0;
     return;
@@ -520,7 +579,7 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
     f2[i * L64P + c] = f64_to_f32(a22[i * L64P + c]);
   }
   __syncthreads();
-  trinv64_f32(f2, f3, f0);
+  trinv64_f32(f2, tcol, f3, f0);
   // ---- X21 = -X22 T (FP32)
   {
     float acc[4][4];
