@@ -61,6 +61,18 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// -x by the sign bit (an integer operation, no FP64 instruction)
+__device__ __forceinline__ double neg_f64(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+// |x| as its bit pattern: for two such patterns integer order is the order of |x|
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
 __device__ __forceinline__ double sgn(double x) { return (x > 0.0) - (x < 0.0); }
 
 // SoftThreshold(v, c) = sign(v) max(|v| - c, 0)  (App. A.1).

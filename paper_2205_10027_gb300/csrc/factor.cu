@@ -256,16 +256,19 @@ constexpr size_t leaf_smem(int nb, size_t elt) { return 2 * (size_t)nb * (nb + 4
 // a_ij / sqrt(d_j)), one lane of warp 0 runs the pivot chain d_{j+1} = a_{j+1,j+1} -
 // a_{j+1,j}^2 / d_j one column ahead, and the six warps on the other three sub-partitions
 // apply the update of column j to the rest of the trailing triangle meanwhile.
-constexpr int L64 = 64, L64P = 65;     // panel size, shared row pitch (odd: conflict-free columns)
+constexpr int L64 = 64, L64P = 65;     // panel size, FP64 row pitch (odd: conflict-free columns)
+constexpr int F64P = 68;               // FP32 row pitch: rows 16-byte aligned for float4 loads
 constexpr int LEAF128_THREADS = 256;
 constexpr size_t leaf128_smem() {
-  return 3 * (size_t)L64 * L64P * sizeof(double) + 5 * (size_t)L64 * L64P * sizeof(float);
+  return 3 * (size_t)L64 * L64P * sizeof(double) + 5 * (size_t)L64 * F64P * sizeof(float);
 }
 
-// 1 / d in FP64 for a pivot d > 0: the PTX approximate reciprocal refined by two Newton-
-// Raphson steps in residual form, e = 1 - d y, y <- y + y e (each step squares the relative
-// error); ~5 FP64 operations instead of a correctly rounded divide's longer sequence, which
-// matters on the pivot chain.
+// 1 / d in FP64 for a pivot d > 0: the PTX approximate reciprocal y (relative error e0 well
+// below 2^-16), refined by one step of the third-order iteration for the reciprocal,
+// e = 1 - d y, y <- y (1 + e + e^2) (the error becomes O(e0^3), below FP64 rounding): three
+// dependent FP64 operations, where two Newton steps take four and a correctly rounded divide
+// longer still.  On this part each dependent FP64 operation costs ~64 cycles, and the pivot
+// chain is the leaf's critical path.
 // A pivot is usable when it is a positive finite number: tested on the bit pattern with
 // integer operations, which keeps FP64 compares (one FP64 instruction each) off the chain.
 __device__ __forceinline__ bool pivot_ok(double d) {
@@ -279,10 +282,8 @@ __device__ __forceinline__ double pivot_reciprocal(double d) {
   if (ex < 63 || ex > 1983) return 1.0 / d;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
-  double e = fma(-d, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-d, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // The lower triangle of a 64 x 64 block in column-major order, (i, c) packed as i | c << 8:
@@ -326,7 +327,6 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, co
     }
     __syncthreads();
     for (int j = c0; j < c1; ++j) {
-      if (*fail) break;
       if (tid == 0 && j + 1 < c1) {
         // the pivot chain, one column ahead
         const double aj = a[(j + 1) * L64P + j];
@@ -402,38 +402,63 @@ __device__ void chol64_f64(double* a, double* piv, double* inv, double* tcol, co
 
 // One joining level of the recursive-doubling inverse: for every pair of W x W diagonal blocks
 // [[X11, 0], [X21, X22]] of X, X21 = -X22 (L21 X11), the two W x W products of all pairs formed
-// at once (T in tmp).
+// at once (T in tmp).  Thread layout: 8W threads per pair, each with one column j and the W / 8
+// rows ib, ib + 8, ...; the k-loops run the full width W (the upper triangles of X and L hold
+// zeros, so the sums equal the triangular ones) with float4 loads along k.
 template <int W>
 __device__ __forceinline__ void trinv_join(const float* l, float* x, float* tmp) {
-  constexpr int OUTS = (L64 / (2 * W)) * W * W;  // outputs of one product over all pairs: 32 W
+  constexpr int R = W / 8;  // rows per thread
   const int tid = threadIdx.x;
-  // T = L21 X11 (X11 lower: k >= j)
-  for (int e = tid; e < OUTS; e += LEAF128_THREADS) {
-    const int pair = e / (W * W), ij = e % (W * W), i = ij / W, j = ij % W;
-    const int o = 2 * W * pair;
-    float sacc = 0.f;
-    for (int k = j; k < W; ++k) sacc = fmaf(l[(o + W + i) * L64P + o + k], x[(o + k) * L64P + o + j], sacc);
-    tmp[(o + W + i) * L64P + o + j] = sacc;
+  const int pair = tid / (8 * W), rem = tid % (8 * W), j = rem % W, ib = rem / W;
+  const int o = 2 * W * pair;
+  float acc[R];
+  // T = L21 X11
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const float b0 = x[(o + k) * F64P + o + j], b1 = x[(o + k + 1) * F64P + o + j];
+    const float b2 = x[(o + k + 2) * F64P + o + j], b3 = x[(o + k + 3) * F64P + o + j];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 a4 = *reinterpret_cast<const float4*>(l + (o + W + ib + 8 * r) * F64P + o + k);
+      acc[r] = fmaf(a4.x, b0, acc[r]);
+      acc[r] = fmaf(a4.y, b1, acc[r]);
+      acc[r] = fmaf(a4.z, b2, acc[r]);
+      acc[r] = fmaf(a4.w, b3, acc[r]);
+    }
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) tmp[(o + W + ib + 8 * r) * F64P + o + j] = acc[r];
   __syncthreads();
-  // X21 = -X22 T (X22 lower: k <= i)
-  for (int e = tid; e < OUTS; e += LEAF128_THREADS) {
-    const int pair = e / (W * W), ij = e % (W * W), i = ij / W, j = ij % W;
-    const int o = 2 * W * pair;
-    float sacc = 0.f;
-    for (int k = 0; k <= i; ++k) sacc = fmaf(x[(o + W + i) * L64P + o + W + k], tmp[(o + W + k) * L64P + o + j], sacc);
-    x[(o + W + i) * L64P + o + j] = -sacc;
+  // X21 = -X22 T
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#pragma unroll
+  for (int k = 0; k < W; k += 4) {
+    const float b0 = tmp[(o + W + k) * F64P + o + j], b1 = tmp[(o + W + k + 1) * F64P + o + j];
+    const float b2 = tmp[(o + W + k + 2) * F64P + o + j], b3 = tmp[(o + W + k + 3) * F64P + o + j];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 a4 = *reinterpret_cast<const float4*>(x + (o + W + ib + 8 * r) * F64P + o + W + k);
+      acc[r] = fmaf(a4.x, b0, acc[r]);
+      acc[r] = fmaf(a4.y, b1, acc[r]);
+      acc[r] = fmaf(a4.z, b2, acc[r]);
+      acc[r] = fmaf(a4.w, b3, acc[r]);
+    }
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[(o + W + ib + 8 * r) * F64P + o + j] = -acc[r];
   __syncthreads();
 }
 
-// X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch L64P), all 256
-// threads, by recursive doubling: the eight 8 x 8 diagonal blocks are inverted by forward
-// substitution (one column per thread, 1 / l_ii from rdiag, the FP64 reciprocal diagonal the
-// panel left), then blocks of width 8, 16, 32 are joined pairwise (trinv_join).  The critical
-// path is the 8-row substitution and three levels of short products instead of 64 dependent
-// rows.  x must be zero on entry (its upper triangle is left so); tmp is 64 x 64 (pitch L64P)
-// scratch.
+// X = L^{-1} in FP32 for the 64 x 64 lower-triangular L (FP32 copy l, pitch F64P, zero upper
+// triangle), all 256 threads, by recursive doubling: the eight 8 x 8 diagonal blocks are
+// inverted by forward substitution (one column per thread, 1 / l_ii from rdiag, the FP64
+// reciprocal square roots of the pivots), then blocks of width 8, 16, 32 are joined pairwise
+// (trinv_join).  The critical path is the 8-row substitution and three levels of short
+// products instead of 64 dependent rows.  x must be zero on entry (its upper triangle is left
+// so); tmp is 64 x 64 (pitch F64P) scratch.
 __device__ void trinv64_f32(const float* l, const double* rdiag, float* x, float* tmp) {
   const int tid = threadIdx.x;
   if (tid < L64) {
@@ -444,12 +469,12 @@ __device__ void trinv64_f32(const float* l, const double* rdiag, float* x, float
     for (int r = 0; r < 8; ++r) {
       float sacc = 0.f;
 #pragma unroll
-      for (int k = 0; k < r; ++k) sacc = fmaf(l[(o + r) * L64P + o + k], xr[k], sacc);
+      for (int k = 0; k < r; ++k) sacc = fmaf(l[(o + r) * F64P + o + k], xr[k], sacc);
       xr[r] = (r < c) ? 0.f : ((r == c ? 1.f : 0.f) - sacc) * (float)rdiag[o + r];
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-      if (r >= c) x[(o + r) * L64P + o + c] = xr[r];
+      if (r >= c) x[(o + r) * F64P + o + c] = xr[r];
   }
   __syncthreads();
   trinv_join<8>(l, x, tmp);
@@ -457,48 +482,69 @@ __device__ void trinv64_f32(const float* l, const double* rdiag, float* x, float
   trinv_join<32>(l, x, tmp);
 }
 
-// acc (4 x 4 block at rows r0, columns c0) = sum_k A(i, k) B(k, j) over k < 64, A(i, k) at
-// a[i * L64P + k]; B(k, j) at b[k * L64P + j], or at b[j * L64P + k] when BT (a transpose).
+// acc[q][p] = sum_k A(row q, k) B(k, col p) over k < 64 for the thread's 16 outputs, A(i, k) at
+// a[i * F64P + k]; B(k, j) at b[k * F64P + j], or at b[j * F64P + k] when BT (a transpose).
+// Rows are mm_row(q) = (tid >> 4) + 16 q; columns mm_col<BT>(p) = (tid & 15) + 16 p when BT
+// (the 16 lanes' B rows then fall in distinct bank groups), 4 (tid & 15) + p otherwise (one
+// float4 of a B row).  Every operand is read as float4 along k or along the B row.
+__device__ __forceinline__ int mm_row(int q) { return (threadIdx.x >> 4) + 16 * q; }
 template <bool BT>
-__device__ __forceinline__ void mm64_4x4(const float* a, const float* b, int r0, int c0, float (&acc)[4][4]) {
+__device__ __forceinline__ int mm_col(int p) { return BT ? (threadIdx.x & 15) + 16 * p : 4 * (threadIdx.x & 15) + p; }
+template <bool BT>
+__device__ __forceinline__ void mm64_4x4(const float* a, const float* b, float (&acc)[4][4]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
-#pragma unroll 8
-  for (int k = 0; k < L64; ++k) {
-    float av[4], bv[4];
+#pragma unroll 4
+  for (int k = 0; k < L64; k += 4) {
+    float av[4][4], bv[4][4];  // av[q][kk] = A(row q, k + kk); bv[kk][p] = B(k + kk, col p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) av[q] = a[(r0 + q) * L64P + k];
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(a + mm_row(q) * F64P + k);
+      av[q][0] = v.x; av[q][1] = v.y; av[q][2] = v.z; av[q][3] = v.w;
+    }
+    if (BT) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) bv[p] = BT ? b[(c0 + p) * L64P + k] : b[k * L64P + c0 + p];
+      for (int p = 0; p < 4; ++p) {
+        const float4 v = *reinterpret_cast<const float4*>(b + mm_col<true>(p) * F64P + k);
+        bv[0][p] = v.x; bv[1][p] = v.y; bv[2][p] = v.z; bv[3][p] = v.w;
+      }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 v = *reinterpret_cast<const float4*>(b + (k + kk) * F64P + mm_col<false>(0));
+        bv[kk][0] = v.x; bv[kk][1] = v.y; bv[kk][2] = v.z; bv[kk][3] = v.w;
+      }
+    }
 #pragma unroll
-      for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(av[q], bv[p], acc[q][p]);
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(av[q][kk], bv[kk][p], acc[q][p]);
   }
 }
 
-__global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64_t ld, double* Xblk, double* ld_part,
+__global__ void __launch_bounds__(LEAF128_THREADS, 1) k_leaf128(double* Ablk, int64_t ld, double* Xblk, double* ld_part,
                                                          int* pd) {
   if (*pd == 0) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  constexpr int M = L64 * L64P;
+  constexpr int M = L64 * L64P, MF = L64 * F64P;
   double* a11 = reinterpret_cast<double*>(sm_raw);  // FP64 panels: A11 -> L11, A21 -> L21, A22 -> L22
   double* a21 = a11 + M;
   double* a22 = a21 + M;
   float* f0 = reinterpret_cast<float*>(a22 + M);    // L11 (FP32), then L21 (FP32)
-  float* f1 = f0 + M;                                // X11
-  float* f2 = f1 + M;                                // A21 (FP32), then L22 (FP32), then X21
-  float* f3 = f2 + M;                                // X22
-  float* f4 = f3 + M;                                // T = L21 X11
+  float* f1 = f0 + MF;                               // X11
+  float* f2 = f1 + MF;                               // A21 (FP32), then L22 (FP32), then X21
+  float* f3 = f2 + MF;                               // X22
+  float* f4 = f3 + MF;                               // T = L21 X11
   __shared__ double piv[2 * L64], inv[L64], tcol[L64];
   __shared__ double red[32];
   __shared__ uint16_t tri[kTri64N];
   __shared__ int fail;
   const int tid = threadIdx.x;
   for (int e = tid; e < kTri64N; e += LEAF128_THREADS) tri[e] = g_tri64[e];
-  const int r0 = (tid >> 4) * 4, c0 = (tid & 15) * 4;  // 4 x 4 output block of the small products
   {
     // every thread issues its 48 loads (16 per 64 x 64 panel) before storing any
     constexpr int PER = L64 * L64 / LEAF128_THREADS;   // 16
@@ -528,44 +574,44 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   }
   for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
     const int i = e >> 6, c = e & 63;
-    f0[i * L64P + c] = f64_to_f32(a11[i * L64P + c]);
-    f2[i * L64P + c] = f64_to_f32(a21[i * L64P + c]);
-    f1[i * L64P + c] = 0.f;
-    f3[i * L64P + c] = 0.f;
+    f0[i * F64P + c] = f64_to_f32(a11[i * L64P + c]);
+    f2[i * F64P + c] = f64_to_f32(a21[i * L64P + c]);
+    f1[i * F64P + c] = 0.f;
+    f3[i * F64P + c] = 0.f;
   }
   __syncthreads();
   trinv64_f32(f0, tcol, f1, f4);
   // ---- L21 = A21 X11^T (FP32), kept in FP64 (a21) and FP32 (f0)
   {
     float acc[4][4];
-    mm64_4x4<true>(f2, f1, r0, c0, acc);
+    mm64_4x4<true>(f2, f1, acc);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        a21[(r0 + q) * L64P + c0 + p] = f32_to_f64(acc[q][p]);
-        f0[(r0 + q) * L64P + c0 + p] = acc[q][p];
+        a21[mm_row(q) * L64P + mm_col<true>(p)] = f32_to_f64(acc[q][p]);
+        f0[mm_row(q) * F64P + mm_col<true>(p)] = acc[q][p];
       }
   }
   __syncthreads();
   // ---- A22 -= L21 L21^T: FP32 product, FP64 subtraction (lower triangle)
   {
     float acc[4][4];
-    mm64_4x4<true>(f0, f0, r0, c0, acc);
+    mm64_4x4<true>(f0, f0, acc);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int p = 0; p < 4; ++p)
-        if (c0 + p <= r0 + q) a22[(r0 + q) * L64P + c0 + p] -= f32_to_f64(acc[q][p]);
+        if (mm_col<true>(p) <= mm_row(q)) a22[mm_row(q) * L64P + mm_col<true>(p)] -= f32_to_f64(acc[q][p]);
   }
   // ---- T = L21 X11 (FP32), independent of the second panel
   {
     float acc[4][4];
-    mm64_4x4<false>(f0, f1, r0, c0, acc);
+    mm64_4x4<false>(f0, f1, acc);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int p = 0; p < 4; ++p) f4[(r0 + q) * L64P + c0 + p] = acc[q][p];
+      for (int p = 0; p < 4; ++p) f4[mm_row(q) * F64P + mm_col<false>(p)] = acc[q][p];
   }
   __syncthreads();
   // ---- second panel: L22 (FP64), X22 (FP32)
@@ -576,19 +622,19 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
   }
   for (int e = tid; e < L64 * L64; e += LEAF128_THREADS) {
     const int i = e >> 6, c = e & 63;
-    f2[i * L64P + c] = f64_to_f32(a22[i * L64P + c]);
+    f2[i * F64P + c] = f64_to_f32(a22[i * L64P + c]);
   }
   __syncthreads();
   trinv64_f32(f2, tcol, f3, f0);
   // ---- X21 = -X22 T (FP32)
   {
     float acc[4][4];
-    mm64_4x4<false>(f3, f4, r0, c0, acc);
+    mm64_4x4<false>(f3, f4, acc);
     __syncthreads();  // every thread has read f2 (L22) before it is overwritten
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int p = 0; p < 4; ++p) f2[(r0 + q) * L64P + c0 + p] = -acc[q][p];
+      for (int p = 0; p < 4; ++p) f2[mm_row(q) * F64P + mm_col<false>(p)] = -acc[q][p];
   }
   // ---- log det = sum of log pivots (FP64)
   const double lsum = (tid < 2 * L64) ? log(piv[tid]) : 0.0;
@@ -604,9 +650,9 @@ __global__ void __launch_bounds__(LEAF128_THREADS) k_leaf128(double* Ablk, int64
     Ar0[L64 + c] = 0.0;                            // upper off-diagonal block
     Ar1[c] = a21[i * L64P + c];                    // L21
     Ar1[L64 + c] = (c <= i) ? a22[i * L64P + c] : 0.0;   // L22
-    if (c <= i) Xr0[c] = f32_to_f64(f1[i * L64P + c]);   // X11
-    Xr1[c] = f32_to_f64(f2[i * L64P + c]);                // X21
-    if (c <= i) Xr1[L64 + c] = f32_to_f64(f3[i * L64P + c]);   // X22
+    if (c <= i) Xr0[c] = f32_to_f64(f1[i * F64P + c]);   // X11
+    Xr1[c] = f32_to_f64(f2[i * F64P + c]);                // X21
+    if (c <= i) Xr1[L64 + c] = f32_to_f64(f3[i * F64P + c]);   // X22
   }
   if (tid == 0) *ld_part = tot;
 }

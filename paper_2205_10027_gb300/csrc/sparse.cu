@@ -13,9 +13,17 @@ namespace glasso {
 namespace {
 constexpr int kRowsPerBlock = 8;  // one warp per row in the CSR passes
 
-// entry (i, j) of A, or of A - Am
-__device__ __forceinline__ double entry(const double* __restrict__ A, const double* __restrict__ Am, int64_t o) {
-  return Am ? A[o] - Am[o] : A[o];
+// Whether entry o of A (of A - Am when Am is given) is stored: A_o != 0, or A_o != Am_o, both
+// decided on the bit patterns with integer instructions only (an FP64 compare or subtraction
+// costs one FP64 instruction per warp, and these passes read every entry of the n x n block).
+// Shifting out the sign bit makes -0 a zero; two patterns that differ and are not both zeros
+// are two different numbers (or a NaN), whose difference is nonzero, so the count is the
+// count of nonzero A - Am and stays within nnz(A) + nnz(Am).
+__device__ __forceinline__ bool stored(const double* __restrict__ A, const double* __restrict__ Am, int64_t o) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(A[o]);
+  if (!Am) return (a << 1) != 0;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(Am[o]);
+  return a != b && ((a | b) << 1) != 0;
 }
 
 // counts[i] = nonzeros of row i of the n x n block (0 for the padding rows)
@@ -27,7 +35,7 @@ __global__ void k_row_counts(const double* __restrict__ A, const double* __restr
   if (i < n) {
     for (int64_t j0 = 0; j0 < n; j0 += 32) {
       const int64_t j = j0 + lane;
-      const bool nz = j < n && entry(A, Am, (int64_t)i * ld + j) != 0.0;
+      const bool nz = j < n && stored(A, Am, (int64_t)i * ld + j);
       c += __popc(__ballot_sync(0xffffffffu, nz));
     }
   }
@@ -69,12 +77,15 @@ __global__ void k_csr_fill(const double* __restrict__ A, const double* __restric
   int64_t base = rowptr[i];
   for (int64_t j0 = 0; j0 < n; j0 += 32) {
     const int64_t j = j0 + lane;
-    const double v = j < n ? entry(A, Am, (int64_t)i * ld + j) : 0.0;
-    const unsigned m = __ballot_sync(0xffffffffu, v != 0.0);
-    if (v != 0.0) {
+    const bool nz = j < n && stored(A, Am, (int64_t)i * ld + j);
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if (nz) {
+      // the difference is formed only for stored entries (one FP64 instruction per warp that
+      // holds any)
+      const int64_t o = (int64_t)i * ld + j;
       const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
       col[pos] = (int)j;
-      val[pos] = v;
+      val[pos] = Am ? A[o] - Am[o] : A[o];
     }
     base += __popc(m);
   }
@@ -93,7 +104,7 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
   const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 32;
   if (lower && c0 > r0 + 31) return;
   __shared__ double tile[32][65];
-  __shared__ double wmax[8];
+  __shared__ unsigned long long wmax[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int rr = warp; rr < 32; rr += 8) {
     const int64_t e0 = rowptr[r0 + rr], e1 = rowptr[r0 + rr + 1];
@@ -105,29 +116,35 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
       a1 = fma(v, b[32 + lane], a1);
     }
     if (RESID) {
+      // I - A B: off the diagonal a sign flip (no FP64 instruction), on it 1 + (-sum), the
+      // same rounding as 1 - sum
       const int64_t i = r0 + rr, j0 = c0 + lane, j1 = c0 + 32 + lane;
-      a0 = ((i == j0 && i < n) ? 1.0 : 0.0) - a0;
-      a1 = ((i == j1 && i < n) ? 1.0 : 0.0) - a1;
+      a0 = neg_f64(a0);
+      a1 = neg_f64(a1);
+      if (i == j0 && i < n) a0 += 1.0;
+      if (i == j1 && i < n) a1 += 1.0;
     }
     tile[rr][lane] = a0;
     tile[rr][32 + lane] = a1;
   }
   __syncthreads();
   if (RESID) {
-    double mx = 0.0;
+    // max |.| on the bit patterns with the sign cleared (integer order = order of |x|, and a
+    // NaN ranks above every number, so it reaches *rmax instead of being skipped)
+    unsigned long long mx = 0;
     for (int rr = warp; rr < 32; rr += 8) {
       if (r0 + rr >= n) break;
-      if (c0 + lane < n) mx = fmax(mx, fabs(tile[rr][lane]));
-      if (c0 + 32 + lane < n) mx = fmax(mx, fabs(tile[rr][32 + lane]));
+      if (c0 + lane < n) mx = umax64(mx, abs_bits(tile[rr][lane]));
+      if (c0 + 32 + lane < n) mx = umax64(mx, abs_bits(tile[rr][32 + lane]));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) wmax[warp] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int w = 0; w < 8; ++w) m = fmax(m, wmax[w]);
-      if (m > 0.0) atomic_max_nonneg(rmax, m);
+      unsigned long long m = 0;
+      for (int w = 0; w < 8; ++w) m = umax64(m, wmax[w]);
+      if (m != 0) atomicMax(reinterpret_cast<unsigned long long*>(rmax), m);
     }
   }
   if (!TRANS) {
