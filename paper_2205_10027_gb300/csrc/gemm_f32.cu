@@ -106,7 +106,16 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmAr
   }
   // alpha acc in FP32; a beta != 0 update (the factorisation's trailing updates) is added to
   // the FP64 C in FP64, so the Schur complement loses nothing beyond the product's own error
+  // (the C entries are all loaded before the first store, so their latencies overlap)
   const float al = (float)p.alpha;
+  double cv[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      cv[i][j] = (p.beta != 0.0 && !(p.lower && c > r)) ? p.C[(int64_t)r * p.ldc + c] : 0.0;
+    }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = row0 + ty + 16 * i;
@@ -114,9 +123,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmAr
     for (int j = 0; j < R; ++j) {
       const int c = col0 + tx + 16 * j;
       if (p.lower && c > r) continue;
-      double* dst = p.C + (int64_t)r * p.ldc + c;
       const double v = f32_to_f64(al * acc[i][j]);
-      *dst = p.beta == 0.0 ? v : fma(p.beta, *dst, v);
+      p.C[(int64_t)r * p.ldc + c] = p.beta == 0.0 ? v : fma(p.beta, cv[i][j], v);
     }
   }
 }

@@ -257,7 +257,10 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   ok = __syncthreads_and(ok);  // uniform: tcgen05.ld below is warp-collective
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int wq = warp & 3;
-  const int c_first = (warp >> 2) * 4, c_end = min(TN / 32, c_first + 4);
+  // warp w reads TMEM lanes 32 (w % 4) ..; with eight warps, w and w + 4 split the tile's
+  // 32-column chunks between them
+  constexpr int CH = TN / 32 / (CF::THREADS / 128);
+  const int c_first = (warp >> 2) * CH, c_end = c_first + CH;
   float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // [32][33] per warp
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(p.err, 1);
@@ -267,7 +270,9 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
     // factorisation) adds it to the FP64 C with one FP64 FMA, so the Schur complement keeps
     // FP64 accuracy apart from the split product's own error.  That is one FP64 operation
     // per output element of a K-long product: ~40 us of FP64 pipe per n = 10^4
-    // factorisation, spread over the whole GPU.
+    // factorisation, spread over the whole GPU.  The 32 C entries a lane updates per chunk are
+    // all loaded before the first is stored, so their latencies overlap instead of adding up
+    // row by row.
     const float al = (float)p.alpha;
 #pragma unroll 1
     for (int c = c_first; c < c_end; ++c) {
@@ -282,13 +287,29 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
       for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];  // row lane, column j
       __syncwarp();
       const int col = col0 + c * 32 + lane;
+      const int rbase = row0 + wq * 32;
+      double* const cbase = p.C + (int64_t)rbase * p.ldc + col;
+      if (p.beta == 0.0) {
 #pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const int r = row0 + wq * 32 + rr;
-        if (r >= p.M || col >= p.N || (p.lower && col > r)) continue;
-        double* dst = p.C + (int64_t)r * p.ldc + col;
-        const double a = f32_to_f64(al * stage[rr * 33 + lane]);
-        *dst = p.beta == 0.0 ? a : fma(p.beta, *dst, a);
+        for (int rr = 0; rr < 32; ++rr) {
+          const int r = rbase + rr;
+          if (r >= p.M || col >= p.N || (p.lower && col > r)) continue;
+          cbase[(int64_t)rr * p.ldc] = f32_to_f64(al * stage[rr * 33 + lane]);
+        }
+      } else {
+        double cv[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+          const int r = rbase + rr;
+          const bool in = r < p.M && col < p.N && !(p.lower && col > r);
+          cv[rr] = in ? cbase[(int64_t)rr * p.ldc] : 0.0;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+          const int r = rbase + rr;
+          if (r >= p.M || col >= p.N || (p.lower && col > r)) continue;
+          cbase[(int64_t)rr * p.ldc] = fma(p.beta, cv[rr], f32_to_f64(al * stage[rr * 33 + lane]));
+        }
       }
       __syncwarp();
     }
@@ -351,49 +372,77 @@ struct SplitJob {
   void* hi;
   void* lo;
   int64_t ldo;
-  int tiles_x;  // 32-column tiles of the output
+  int tiles_x;  // 64-column tiles of the output
+  int vec;      // rows of src are 16-byte aligned (source read as double2)
 };
 
-// blockIdx.z selects the job: the A and B operands of a product are split in one launch.
+// blockIdx.z selects the job: the A and B operands of a product are split in one launch.  A
+// block covers 32 rows x 64 columns of the output (K, the column count, is a multiple of 64);
+// lane tx owns columns 2 tx and 2 tx + 1 and reads them as one 16-byte load when the source
+// allows it (op not transposed, 16-byte aligned rows), else through a shared-memory transpose;
+// each hi / lo pair of columns leaves as one 4-byte (BF16) or 8-byte (TF32) store.
 template <bool BF16>
-__global__ void k_split(const __grid_constant__ SplitJob ja, const __grid_constant__ SplitJob jb) {
+__device__ __forceinline__ void split_store(const SplitJob& j, int64_t o, double x0, double x1) {
+  uint32_t h0, l0, h1, l1;
+  if (BF16) {
+    split_bits<8>(x0, h0, l0);
+    split_bits<8>(x1, h1, l1);
+    reinterpret_cast<uint32_t*>(j.hi)[o >> 1] = (h0 >> 16) | (h1 & 0xFFFF0000u);
+    reinterpret_cast<uint32_t*>(j.lo)[o >> 1] = (l0 >> 16) | (l1 & 0xFFFF0000u);
+  } else {
+    split_bits<11>(x0, h0, l0);
+    split_bits<11>(x1, h1, l1);
+    reinterpret_cast<uint2*>(j.hi)[o >> 1] = make_uint2(h0, h1);
+    reinterpret_cast<uint2*>(j.lo)[o >> 1] = make_uint2(l0, l1);
+  }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_split(const __grid_constant__ SplitJob ja, const __grid_constant__ SplitJob jb) {
   const SplitJob& j = blockIdx.z == 0 ? ja : jb;
   const int tiles_y = (j.rows_out + 31) / 32;
   if ((int)blockIdx.x >= j.tiles_x || (int)blockIdx.y >= tiles_y) return;
-  __shared__ double t[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int c = c0 + 2 * tx;                     // this lane's two columns c, c + 1
   const double* __restrict__ src = j.src;
-  for (int i = ty; i < 32; i += 8) {
-    // load the (r0, c0) tile of op: element (r0 + i, c0 + tx) of op
-    double v = 0.0;
-    if (!j.trans) {
-      const int rr = r0 + i, cc = c0 + tx;
-      if (rr < j.rows && cc < j.cols) v = src[(int64_t)rr * j.lds + cc];
-      t[i][tx] = v;
-    } else {
-      // op[r][c] = src[c][r]: read src row c0 + i, columns r0 + tx (coalesced)
-      const int sr = c0 + i, sc = r0 + tx;
-      if (sr < j.cols && sc < j.rows) v = src[(int64_t)sr * j.lds + sc];
-      t[tx][i] = v;
+  if (!j.trans && j.vec) {
+    double2 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty + 8 * i;
+      v[i] = (r < j.rows) ? *reinterpret_cast<const double2*>(src + (int64_t)r * j.lds + c) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty + 8 * i;
+      if (r < j.rows_out) split_store<BF16>(j, (int64_t)r * j.ldo + c, v[i].x, v[i].y);
+    }
+    return;
+  }
+  __shared__ double t[32][65];  // t[r][c - c0]
+  if (!j.trans) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty + 8 * i;
+      const bool in = r < j.rows;
+      t[ty + 8 * i][2 * tx] = in ? src[(int64_t)r * j.lds + c] : 0.0;
+      t[ty + 8 * i][2 * tx + 1] = in ? src[(int64_t)r * j.lds + c + 1] : 0.0;
+    }
+  } else {
+    // op[r][c] = src[c][r]: src rows c0 .. c0 + 63, columns r0 + tx (coalesced)
+    const int r = r0 + tx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int sr = c0 + ty + 8 * i;
+      t[tx][ty + 8 * i] = (r < j.rows) ? src[(int64_t)sr * j.lds + r] : 0.0;
     }
   }
   __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int rr = r0 + i, cc = c0 + tx;
-    if (rr >= j.rows_out || cc >= j.cols) continue;
-    const double x = t[i][tx];
-    const int64_t o = (int64_t)rr * j.ldo + cc;
-    uint32_t h, l;
-    if (BF16) {
-      split_bits<8>(x, h, l);
-      reinterpret_cast<uint16_t*>(j.hi)[o] = (uint16_t)(h >> 16);
-      reinterpret_cast<uint16_t*>(j.lo)[o] = (uint16_t)(l >> 16);
-    } else {
-      split_bits<11>(x, h, l);
-      reinterpret_cast<uint32_t*>(j.hi)[o] = h;
-      reinterpret_cast<uint32_t*>(j.lo)[o] = l;
-    }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 8 * i;
+    if (r < j.rows_out) split_store<BF16>(j, (int64_t)r * j.ldo + c, t[ty + 8 * i][2 * tx], t[ty + 8 * i][2 * tx + 1]);
   }
 }
 
@@ -437,7 +486,9 @@ CUtensorMap make_map(void* base, bool bf16, int rows, int cols, int64_t ld, int 
 
 SplitJob split_job(const double* src, int64_t lds, int rows, int rows_out, int cols, bool trans, void* hi,
                    void* lo, int64_t ldo) {
-  return SplitJob{src, lds, rows, rows_out, cols, trans ? 1 : 0, hi, lo, ldo, (cols + 31) / 32};
+  if (cols % 64 || ldo % 2) throw Error(GLASSO_ERR_ARG, "split: K must be a multiple of 64");
+  const bool vec = (reinterpret_cast<uintptr_t>(src) % 16) == 0 && lds % 2 == 0;
+  return SplitJob{src, lds, rows, rows_out, cols, trans ? 1 : 0, hi, lo, ldo, cols / 64, vec ? 1 : 0};
 }
 
 // Both jobs in one launch; jobs == 1 runs only the first.
