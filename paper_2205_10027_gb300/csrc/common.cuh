@@ -119,6 +119,7 @@ __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 
 #include <stdexcept>
 #include <string>
+#include <utility>
 namespace glasso {
 // Host code reports failures by throwing Error; the C ABI turns it into a status code.
 struct Error : std::runtime_error {
@@ -144,3 +145,34 @@ extern thread_local int64_t tl_launches;
     ++::glasso::tl_launches;              \
     CUDA_CHECK(cudaGetLastError());       \
   } while (0)
+
+// ---- programmatic dependent launch ---------------------------------------------------------
+// The factorisation and the products are long chains of dependent launches, many of them a few
+// microseconds long.  A kernel launched through launch_dependent() may be scheduled while the
+// kernel before it on the stream is still running: it calls dep_wait() before its first access
+// to global memory (griddepcontrol.wait: returns once the previous kernel has completed and its
+// writes are visible; a no-op for a kernel launched the ordinary way), then dep_release()
+// (griddepcontrol.launch_dependents), which lets the next such kernel be scheduled in turn.  So
+// the launch latency and the block scheduling of each kernel overlap the end of the one before.
+// GLASSO_NO_PDL=1 launches them the ordinary way.
+namespace glasso {
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+bool pdl_enabled();
+template <typename... Params, typename... Args>
+inline void launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  CUDA_CHECK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+  ++tl_launches;
+}
+}  // namespace glasso

@@ -207,6 +207,14 @@ void Workspace::ensure(int64_t n_new, size_t budget) {
 thread_local int64_t tl_launches = 0;
 int64_t thread_launches() { return tl_launches; }
 
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GLASSO_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
     cudaEvent_t e = pool.back();

@@ -105,6 +105,8 @@ __global__ void __launch_bounds__(PT) k_leaf_chol_inv(double* Ablk, int64_t ld, 
   constexpr int NW = PT / 32;
   constexpr unsigned FULL = 0xffffffffu;
   static_assert(NB % 32 == 0 && PT % 32 == 0, "shape");
+  dep_wait();
+  dep_release();
   if (*pd == 0) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* a = reinterpret_cast<T*>(sm_raw);  // [NB][LDS]: L (lower); T_pj scratch above the diagonal
@@ -276,14 +278,20 @@ __device__ __forceinline__ bool pivot_ok(double d) {
   return b > 0 && ((b >> 52) & 0x7FF) != 0x7FF;  // sign clear, not +0, not Inf or NaN
 }
 
+// The divide for pivots outside [2^-960, 2^960], kept out of line so that the compiler cannot
+// evaluate it speculatively on the chain (a divide is a long sequence of FP64 operations).
+__device__ __noinline__ double pivot_reciprocal_slow(double d) { return 1.0 / d; }
+
 __device__ __forceinline__ double pivot_reciprocal(double d) {
-  // outside [2^-960, 2^960] (exponent field tested as an integer) take the divide
-  const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
-  if (ex < 63 || ex > 1983) return 1.0 / d;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
   const double e = fma(-d, y, 1.0);
-  return fma(y, fma(e, e, e), y);
+  double r = fma(y, fma(e, e, e), y);
+  // the range test on the exponent field runs on the integer pipe alongside the FP64
+  // operations instead of before them
+  const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
+  if (ex < 63 || ex > 1983) r = pivot_reciprocal_slow(d);
+  return r;
 }
 
 // The lower triangle of a 64 x 64 block in column-major order, (i, c) packed as i | c << 8:
@@ -528,6 +536,8 @@ __device__ __forceinline__ void mm64_4x4(const float* a, const float* b, float (
 
 __global__ void __launch_bounds__(LEAF128_THREADS, 1) k_leaf128(double* Ablk, int64_t ld, double* Xblk, double* ld_part,
                                                          int* pd) {
+  dep_wait();
+  dep_release();
   if (*pd == 0) return;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int M = L64 * L64P, MF = L64 * F64P;
@@ -659,6 +669,8 @@ __global__ void __launch_bounds__(LEAF128_THREADS, 1) k_leaf128(double* Ablk, in
 
 // out = sum of parts[0..n) in index order (one thread: n is at most a few hundred).
 __global__ void k_sum_parts(const double* parts, int n, const int* pd, double* out) {
+  dep_wait();
+  dep_release();
   if (threadIdx.x != 0) return;
   double s = 0.0;
   for (int i = 0; i < n; ++i) s += parts[i];
@@ -668,6 +680,8 @@ __global__ void k_sum_parts(const double* parts, int n, const int* pd, double* o
 // dst[rows x cols] := src[rows x cols] (both with leading dimension ld), unless *flag == 0.
 __global__ void k_copy_block(const double* __restrict__ src, double* __restrict__ dst, int64_t ld,
                              int rows, int cols, const int* flag) {
+  dep_wait();
+  dep_release();
   if (*flag == 0) return;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
     for (int c = threadIdx.x; c < cols; c += blockDim.x) dst[r * ld + c] = src[r * ld + c];
@@ -736,15 +750,14 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
     double* part = c.ld_parts + o / c.leaf;
     switch (c.kind) {
       case LeafKind::F64Chol:
-        k_leaf128<<<1, LEAF128_THREADS, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+        launch_dependent(k_leaf128, 1, LEAF128_THREADS, c.smem, c.st, Ab, c.ld, Xb, part, c.pd);
         break;
       case LeafKind::F32:
-        k_leaf_chol_inv<float, NB32, 4 * NB32><<<1, 4 * NB32, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+        launch_dependent(k_leaf_chol_inv<float, NB32, 4 * NB32>, 1, 4 * NB32, c.smem, c.st, Ab, c.ld, Xb, part, c.pd);
         break;
       default:
-        k_leaf_chol_inv<double, NB, 4 * NB><<<1, 4 * NB, c.smem, c.st>>>(Ab, c.ld, Xb, part, c.pd);
+        launch_dependent(k_leaf_chol_inv<double, NB, 4 * NB>, 1, 4 * NB, c.smem, c.st, Ab, c.ld, Xb, part, c.pd);
     }
-    LAUNCH_CHECK();
     return;
   }
   const int s1 = split_point(s, c.leaf), s2 = s - s1;
@@ -765,8 +778,7 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
   a.flag = c.pd;
   (*c.gemm)(a, GemmRole::Panel, c.st);
   if (!in_place) {
-    k_copy_block<<<std::min(s2, 1024), 256, 0, c.st>>>(c.T, A21, ld, s2, s1, c.pd);
-    LAUNCH_CHECK();
+    launch_dependent(k_copy_block, std::min(s2, 1024), 256, 0, c.st, c.T, A21, ld, s2, s1, c.pd);
   }
   // X21 = -X22 (L21 X11).  With a side stream and in-place tensor-core products, the first
   // factor L21 X11 is formed into X21 on the side stream right away: it needs only L21 and
@@ -856,8 +868,7 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
       gemm(b, GemmRole::Trailing, st);
     }
   }
-  k_sum_parts<<<1, 32, 0, st>>>(ld_parts, np / leaf, pd, logdet);
-  LAUNCH_CHECK();
+  launch_dependent(k_sum_parts, 1, 32, 0, st, ld_parts, np / leaf, pd, logdet);
 }
 
 void factorisation_products(int np, bool split, LeafKind kind, std::vector<GemmArgs>& out) {

@@ -64,6 +64,8 @@ __device__ __forceinline__ void stage_operand(const double* __restrict__ G, int6
 // stores and the strided reads hit distinct banks): a product this small is latency-bound,
 // so every global load of the block is issued before the first multiply.
 __global__ void __launch_bounds__(256) k_gemm_f32(const __grid_constant__ GemmArgs p) {
+  dep_wait();
+  dep_release();
   if (p.flag && *p.flag == 0) return;
   const int row0 = blockIdx.y * TILE, col0 = blockIdx.x * TILE;
   if (p.lower && row0 + TILE <= col0) return;
@@ -143,8 +145,7 @@ void gemm_f32(const GemmArgs& a, cudaStream_t st) {
   std::call_once(once, [] {
     CUDA_CHECK(cudaFuncSetAttribute(k_gemm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(KMAX)));
   });
-  k_gemm_f32<<<dim3(a.N / TILE, a.M / TILE), 256, smem_for(a.K), st>>>(a);
-  LAUNCH_CHECK();
+  launch_dependent(k_gemm_f32, dim3(a.N / TILE, a.M / TILE), 256, smem_for(a.K), st, a);
 }
 
 }  // namespace glasso

@@ -12,6 +12,8 @@ constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256;
 
 // C[M,N] = alpha * op(A)[M,K] op(B)[K,N] + beta * C  for one 64x64 output tile per block.
 __global__ void __launch_bounds__(THREADS) k_gemm_f64(const __grid_constant__ GemmArgs p) {
+  dep_wait();
+  dep_release();
   if (p.flag && *p.flag == 0) return;  // an earlier step failed (non-PD pivot)
   const int tm = blockIdx.y, tn = blockIdx.x;
   if (p.lower && tm < tn) return;
@@ -96,8 +98,7 @@ void gemm_f64(const GemmArgs& a, int batch, cudaStream_t st) {
   if (a.M % BM || a.N % BN || a.K % BK)
     throw Error(1, "gemm_f64: M, N must be multiples of 64 and K of 16");
   dim3 grid(a.N / BN, a.M / BM, batch);
-  k_gemm_f64<<<grid, THREADS, 0, st>>>(a);
-  LAUNCH_CHECK();
+  launch_dependent(k_gemm_f64, grid, THREADS, 0, st, a);
 }
 
 }  // namespace glasso

@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(CF::THREADS, 1)
   constexpr int TN = CF::TN, STAGES = CF::STAGES, STAGE_BYTES = CF::STAGE_BYTES;
   constexpr int A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
   constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
+  dep_wait();
+  dep_release();
   if (p.flag && *p.flag == 0) return;
   // grouped tile order: consecutive blocks walk down a column of GROUP_M tiles, so the
   // CTAs resident at one time cover a near-square patch and share operand panels in L2
@@ -399,6 +401,8 @@ __device__ __forceinline__ void split_store(const SplitJob& j, int64_t o, double
 
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_split(const __grid_constant__ SplitJob ja, const __grid_constant__ SplitJob jb) {
+  dep_wait();
+  dep_release();
   const SplitJob& j = blockIdx.z == 0 ? ja : jb;
   const int tiles_y = (j.rows_out + 31) / 32;
   if ((int)blockIdx.x >= j.tiles_x || (int)blockIdx.y >= tiles_y) return;
@@ -495,10 +499,9 @@ SplitJob split_job(const double* src, int64_t lds, int rows, int rows_out, int c
 void split2(const SplitJob& a, const SplitJob& b, bool bf16, cudaStream_t st, int jobs = 2) {
   dim3 grid(std::max(a.tiles_x, b.tiles_x), (std::max(a.rows_out, b.rows_out) + 31) / 32, jobs);
   if (bf16)
-    k_split<true><<<grid, dim3(32, 8), 0, st>>>(a, b);
+    launch_dependent(k_split<true>, grid, dim3(32, 8), 0, st, a, b);
   else
-    k_split<false><<<grid, dim3(32, 8), 0, st>>>(a, b);
-  LAUNCH_CHECK();
+    launch_dependent(k_split<false>, grid, dim3(32, 8), 0, st, a, b);
 }
 
 int* g_err = nullptr;     // device error word of the tensor-core kernels
@@ -585,8 +588,7 @@ void tc_gemm_cfg(const GemmArgs& a, bool bf16, void* scratch, size_t scratch_byt
   p.err = g_err;
   p.no_loads = g_no_loads ? 1 : 0;
   dim3 grid(((a.N + TN - 1) / TN) * ((a.M + TM - 1) / TM));
-  k_gemm_tc<CF><<<grid, CF::THREADS, CF::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, p);
-  LAUNCH_CHECK();
+  launch_dependent(k_gemm_tc<CF>, grid, CF::THREADS, CF::SMEM_BYTES, st, mAh, mAl, mBh, mBl, p);
 }
 }  // namespace
 
