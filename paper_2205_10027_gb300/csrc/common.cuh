@@ -19,6 +19,7 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // written by exactly one kernel.
 struct Scalars {
   double z_l1, a_l1, z_fro2, nnz;      // gradient pass
+  double m_free;                       // gradient pass: entries of the free set M (n x n)
   double lin_s, lin_l1;                // trial pass: <S, dA> and sum(|At| - |A|)
   double trsa_t, l1_t, nnz_t;          // trial pass: tr(S At), ||At||_1, nnz(At)
   double logdet_t;                     // Cholesky of the trial point

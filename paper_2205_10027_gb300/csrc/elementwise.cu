@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(RT) k_gradient(const double* __restrict__ S,
                                                  double* __restrict__ parts) {
   __shared__ double red[32];
   double s_z = 0.0, s_a = 0.0, s_z2 = 0.0;
-  int64_t n_nz = 0;
+  int64_t n_nz = 0, n_m = 0;
   const uint64_t lam_bits = (uint64_t)__double_as_longlong(lam);
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double2* s2 = reinterpret_cast<const double2*>(S + i * ld);
@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(RT) k_gradient(const double* __restrict__ S,
         double x = 0.0;
         signed char G = 0;
         if (in_m) {
+          ++n_m;
           G = a_nz ? (signbit(a) ? -1 : 1) : (signbit(g) ? 1 : -1);
           x = g + lam * (double)G;
           s_z += fabs(x);
@@ -139,9 +140,10 @@ __global__ void __launch_bounds__(RT) k_gradient(const double* __restrict__ S,
   const double t1 = block_sum(s_a, red);
   const double t2 = block_sum(s_z2, red);
   const double t3 = block_sum((double)n_nz, red);
+  const double t4 = block_sum((double)n_m, red);
   if (threadIdx.x == 0) {
-    double* p = parts + (int64_t)blockIdx.x * 4;
-    p[0] = t0; p[1] = t1; p[2] = t2; p[3] = t3;
+    double* p = parts + (int64_t)blockIdx.x * 5;
+    p[0] = t0; p[1] = t1; p[2] = t2; p[3] = t3; p[4] = t4;
   }
 }
 
@@ -504,11 +506,11 @@ void pad_identity(double* A, int64_t ld, int64_t n, int np, cudaStream_t st) {
 }
 
 void gradient(const double* S, const double* W, const double* A, int64_t ld, int64_t n, double lam,
-              double* X, int8_t* code, int64_t ldc, double* parts, double* out4, cudaStream_t st) {
+              double* X, int8_t* code, int64_t ldc, double* parts, double* out5, cudaStream_t st) {
   const int g = red_blocks(n);
   k_gradient<<<g, RT, 0, st>>>(S, W, A, ld, n, lam, X, code, ldc, parts);
   LAUNCH_CHECK();
-  k_finalize<<<1, RT, 0, st>>>(parts, g, 4, out4);
+  k_finalize<<<1, RT, 0, st>>>(parts, g, 5, out5);
   LAUNCH_CHECK();
 }
 

@@ -16,9 +16,10 @@ void load_symmetric(const void* src, bool f32, int64_t n, double* dst, int64_t l
 // A[i][i] = 1/(S_ii + lam) for i < n, 1 on the padding (A zero elsewhere beforehand).
 void init_diag(const double* S, int64_t ld, int64_t n, int np, double lam, double* A, cudaStream_t st);
 void pad_identity(double* A, int64_t ld, int64_t n, int np, cudaStream_t st);
-// K1: X, code and out4 = {||Z||_1, ||A||_1, ||Z||_F^2, nnz(A)}; parts >= 4 * kRedBlocks.
+// K1: X, code and out5 = {||Z||_1, ||A||_1, ||Z||_F^2, nnz(A), |M|} (|M| the free-set entries
+// of the n x n matrix); parts >= 5 * kRedBlocks.
 void gradient(const double* S, const double* W, const double* A, int64_t ld, int64_t n, double lam,
-              double* X, int8_t* code, int64_t ldc, double* parts, double* out4, cudaStream_t st);
+              double* X, int8_t* code, int64_t ldc, double* parts, double* out5, cudaStream_t st);
 // K3: At (full), Lt (lower) and out5 = {<S, At - A>, sum(|At| - |A|), tr(S At), ||At||_1, nnz(At)}.
 void trial(const double* A, const double* Y, const int8_t* code, int64_t ldc, const double* S,
            int64_t ld, int64_t n, int np, double lam, double t, double* At, double* Lt,

@@ -325,6 +325,17 @@ Engine::~Engine() {
   if (side_.st) cudaStreamDestroy(side_.st);
   if (side_.fork) cudaEventDestroy(side_.fork);
   if (side_.join) cudaEventDestroy(side_.join);
+  if (t2_.st) {
+    cudaStreamSynchronize(t2_.st);
+    cudaStreamDestroy(t2_.st);
+  }
+  if (t2_.fork) cudaEventDestroy(t2_.fork);
+  if (t2_.join) cudaEventDestroy(t2_.join);
+  if (fac_.st) {
+    cudaStreamSynchronize(fac_.st);
+    cudaStreamDestroy(fac_.st);
+  }
+  if (fac_.join) cudaEventDestroy(fac_.join);
   ws.release();
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
 }
@@ -659,18 +670,19 @@ bool Engine::ensure_csr_of_A(cudaStream_t st) {
 // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3), E similar to
 // Q = (At - A) W; (At - A) is nonzero only where the step changed an entry, so Q is a sparse-
 // dense product (through a CSR of the difference when at most nnz_bound entries fit).
-void Engine::logdet_terms(double nnz_bound, cudaStream_t st) {
+void Engine::logdet_terms(double nnz_bound, cudaStream_t st, double* Q) {
   const int64_t n = st_.n;
+  if (!Q) Q = ws.T;
   Profiler::Rec rec;
   prof.begin_rec(GLASSO_PROF_LOGDET2, 32.0 * (double)n * (double)n, st, rec);
   if (nnz_bound <= (double)ws.csr.cap) {
     csr_valid_ = false;  // the CSR buffers now hold the difference
     csr_rowptr(ws.At, ws.A, ws.ld, n, ws.np, ws.counts, ws.csr.rowptr, st);
     csr_fill(ws.At, ws.A, ws.ld, n, ws.np, ws.csr, st);
-    spmm(ws.csr, ws.W, ws.ld, ws.T, ws.ld, ws.np, false, false, st);
-    trace_terms(ws.T, ws.ld, n, ws.np, ws.parts, &ws.sc->tr_e, st);
+    spmm(ws.csr, ws.W, ws.ld, Q, ws.ld, ws.np, false, false, st);
+    trace_terms(Q, ws.ld, n, ws.np, ws.parts, &ws.sc->tr_e, st);
   } else {
-    logdet_difference_terms(ws.At, ws.A, ws.W, ws.ld, n, ws.np, ws.T, ws.parts, &ws.sc->tr_e, st);
+    logdet_difference_terms(ws.At, ws.A, ws.W, ws.ld, n, ws.np, Q, ws.parts, &ws.sc->tr_e, st);
   }
   prof.end_rec(rec, st);
 }
@@ -920,6 +932,29 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
   double t = 1.0, dF = INFINITY;
   int trials = 0, tier = 1;
   bool accepted = false;
+  // Once a line search has needed the second-order difference (the split-precision forms near
+  // convergence, where the decrease is below the rounding allowance), it is formed for every
+  // trial on a second stream while the trial point is factored: it needs only At, A and W, and
+  // the factorisation leaves most of the GPU idle.  Its product goes to X (free once the
+  // sandwich has used it) instead of the factorisation's scratch T; supp(At - A) lies in the
+  // free set M, so |M| bounds the difference's CSR.
+  static const bool spec_off = [] {  // GLASSO_NO_SPEC_TIER2=1: form it only when needed, in line
+    const char* e = std::getenv("GLASSO_NO_SPEC_TIER2");
+    return e && e[0] == '1';
+  }();
+  const bool spec = !spec_off && cfg_.precision != GLASSO_FP64 && st_.band_hit && h.m_free <= (double)ws.csr.cap;
+  if (spec && !t2_.st) {
+    // the factorisation goes to a stream of the highest priority, so that its one-CTA leaves
+    // and small products take the SMs they need first and the tier-2 kernels fill the rest
+    int lo = 0, hi = 0;
+    CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CUDA_CHECK(cudaStreamCreateWithFlags(&t2_.st, cudaStreamNonBlocking));
+    CUDA_CHECK(cudaEventCreateWithFlags(&t2_.fork, cudaEventDisableTiming));
+    CUDA_CHECK(cudaEventCreateWithFlags(&t2_.join, cudaEventDisableTiming));
+    CUDA_CHECK(cudaStreamCreateWithPriority(&fac_.st, cudaStreamNonBlocking, hi));
+    CUDA_CHECK(cudaEventCreateWithFlags(&fac_.join, cudaEventDisableTiming));
+  }
+  bool band_hit = false;
   auto try_step = [&](double tt) -> double {
     {
       Profiler::Rec rec;
@@ -928,7 +963,19 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
             &ws.sc->lin_s, st);
       prof.end_rec(rec, st);
     }
-    factor(ws.Lt, ws.Lti, st);
+    if (spec) {
+      CUDA_CHECK(cudaEventRecord(t2_.fork, st));
+      CUDA_CHECK(cudaStreamWaitEvent(fac_.st, t2_.fork, 0));
+      CUDA_CHECK(cudaStreamWaitEvent(t2_.st, t2_.fork, 0));
+      factor(ws.Lt, ws.Lti, fac_.st);
+      CUDA_CHECK(cudaEventRecord(fac_.join, fac_.st));
+      logdet_terms(h.m_free, t2_.st, ws.X);
+      CUDA_CHECK(cudaEventRecord(t2_.join, t2_.st));
+      CUDA_CHECK(cudaStreamWaitEvent(st, fac_.join, 0));
+      CUDA_CHECK(cudaStreamWaitEvent(st, t2_.join, 0));
+    } else {
+      factor(ws.Lt, ws.Lti, st);
+    }
     sync_scalars();
     ++trials;
     tier = 1;
@@ -936,9 +983,12 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
     const double lin = h.lin_s + lam * h.lin_l1;
     double d = -(h.logdet_t - st_.ld_A) + lin;
     if (std::fabs(d) <= kDiffBand * delta) {
+      band_hit = true;
       // log det At - log det A = log det(I + E) = tr E - tr E^2 / 2 + O(|E|^3)
-      logdet_terms(h.nnz + h.nnz_t, st);
-      sync_scalars();
+      if (!spec) {
+        logdet_terms(h.nnz + h.nnz_t, st);
+        sync_scalars();
+      }
       // the series is used while |E|_F <= 0.1, where its truncation (<= |E|_F^3 / 2.7) stays
       // far below the second-order term; otherwise the Cholesky difference stands
       if (h.tr_e2 <= 0.01) {
@@ -976,6 +1026,7 @@ int Engine::step(double tol, int max_iter, bool keep_trace) {
     dF = try_step(t);
     accepted = dF < 0.0;
   }
+  st_.band_hit = band_hit;
   out.trials += trials;
   out.step_t = t;
   out.step_dF = dF;

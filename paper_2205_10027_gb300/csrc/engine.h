@@ -73,6 +73,7 @@ struct SolveState {
   double lam = 0, ld_A = 0, trsa = 0, l1 = 0, F = 0;
   double t_last = 1.0;   // G-ISTA: the last accepted step
   int k = 0;
+  bool band_hit = false;  // a trial of the last line search fell in the rounding band
   SolveOut out;
   std::chrono::steady_clock::time_point t_begin;
   int64_t launches_begin = 0;
@@ -167,7 +168,7 @@ class Engine {
   bool csr_valid_ = false;
   bool w_valid_ = false;  // ws.W holds the inverse of ws.A (refined in the split-precision forms)
   // Q = (At - A) W and {tr Q, tr Q^2} into the scalars
-  void logdet_terms(double nnz_bound, cudaStream_t st);
+  void logdet_terms(double nnz_bound, cudaStream_t st, double* Q = nullptr);
   void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);
@@ -198,6 +199,8 @@ class Engine {
   int panel_ = 0;
   cudaStream_t cap_stream_ = nullptr;
   SideStream side_;  // the factorisation's second stream (split-precision forms)
+  SideStream t2_;    // the tier-2 terms formed alongside a trial's factorisation
+  SideStream fac_;   // high-priority stream the trial is factored on meanwhile
   void drop_graphs();
   void factor_direct(double* L, double* Li, cudaStream_t st);
   void factor_graphed(double* L, double* Li, cudaStream_t st);
