@@ -151,13 +151,13 @@ def oracle_full_iteration(side: int, m: int):
 # pipe; byte classes on HBM.
 CLASS_BOUND = {"factor": "tensor", "inverse": "tensor", "refine": "tensor", "sandwich": "tensor",
                "trailing": "tensor", "panel": "tensor", "spmm": "fp64",
-               "gradient": "hbm", "trial": "hbm", "residual": "hbm", "logdet2": "hbm", "aux": "hbm"}
+               "gradient": "hbm", "trial": "hbm", "residual": "fp64", "logdet2": "hbm", "aux": "hbm"}
 CLASS_UNIT = {"factor": "whole Cholesky-with-inverse factorisations (one CUDA graph each: k_gemm_tc, k_split, "
                         "k_gemm_f32, k_leaf128 in the split-precision forms, k_leaf_chol_inv in FP64)",
               "inverse": "W = X^T X (k_gemm_tc)", "refine": "refinement product W R (k_gemm_tc)",
               "sandwich": "dense sandwich products (k_gemm_tc)", "spmm": "sparse sandwich products (k_spmm)",
               "gradient": "gradient pass (k_gradient)", "trial": "trial-point pass (k_trial)",
-              "residual": "FP64 residual I - Theta W (k_spmm residual epilogue)",
+              "residual": "FP64 residual I - Theta W (k_spmm residual epilogue; 2 nnz(Theta) n FP64 FLOPs)",
               "logdet2": "second-order log-det difference (CSR of dTheta, k_spmm, k_trace_pairs)",
               "aux": "symmetrising copies (k_mirror_lower, k_add_lower_mirror)"}
 

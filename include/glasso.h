@@ -201,7 +201,7 @@ enum {
   GLASSO_PROF_FACTOR = 7,     /* whole Cholesky-with-inverse calls (their products included):
                                  FLOPs n^3/3 + n^3/3 */
   GLASSO_PROF_RESIDUAL = 8,   /* mixed mode: FP64 residual I - Theta W from the sparse rows of
-                                 Theta: bytes of the Theta read and the residual write */
+                                 Theta: FP64 FLOPs, 2 nnz(Theta) per column of W */
   GLASSO_PROF_LOGDET2 = 9,    /* second-order log-det difference near the decision boundary:
                                  bytes of the dTheta W and trace passes */
   GLASSO_PROF_AUX = 10,       /* symmetrising copies of W and the refinement update: bytes */

@@ -167,12 +167,25 @@ __global__ void __launch_bounds__(RT) k_trial(const double* __restrict__ A,
     int bi, bj;
     tri_tile(tt, bi, bj);
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
+    // the tile's A and code entries of this thread's four rows are loaded before any is used
+    // (eight independent loads in flight per thread)
+    double av[4];
+    int cv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = (int64_t)bi * 32 + ty + 8 * q, j = (int64_t)bj * 32 + tx;
+      const bool in = i < n && j < n;
+      av[q] = in ? A[i * ld + j] : 0.0;
+      cv[q] = in ? code[i * ldc + j] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
       const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
       double at;
       if (i < n && j < n) {
-        const double a = A[i * ld + j];
-        const int cd = code[i * ldc + j];
+        const double a = av[q];
+        const int cd = cv[q];
         at = a;
         if (cd != 0 && j <= i) {
           const double di = A[i * ld + i], dj = A[j * ld + j];

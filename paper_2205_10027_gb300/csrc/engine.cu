@@ -628,7 +628,8 @@ void Engine::refine_inverse(cudaStream_t st) {
       // the residual is a sparse-dense product: through the CSR of A when it fits
       const bool csr = ensure_csr_of_A(st);
       Profiler::Rec rec;
-      prof.begin_rec(GLASSO_PROF_RESIDUAL, 16.0 * nn, st, rec);
+      // FP64-pipe bound: 2 nnz(A) FLOPs per column of W
+      prof.begin_rec(GLASSO_PROF_RESIDUAL, 2.0 * (double)csr_nnz_ * (double)np, st, rec);
       if (csr) {
         CUDA_CHECK(cudaMemsetAsync(rmax, 0, sizeof(double), st));
         spmm_residual(ws.csr, ws.W, ld, ws.T, ld, ws.n, np, rmax, st);
@@ -661,6 +662,7 @@ bool Engine::ensure_csr_of_A(cudaStream_t st) {
   int64_t nnz = 0;
   CUDA_CHECK(cudaMemcpyAsync(&nnz, ws.csr.rowptr + ws.np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(wait_stream(st));
+  csr_nnz_ = nnz;
   if (nnz > ws.csr.cap) return false;
   csr_fill(ws.A, nullptr, ws.ld, ws.n, ws.np, ws.csr, st);
   csr_valid_ = true;

@@ -169,6 +169,7 @@ class Engine {
   bool w_valid_ = false;  // ws.W holds the inverse of ws.A (refined in the split-precision forms)
   // Q = (At - A) W and {tr Q, tr Q^2} into the scalars
   void logdet_terms(double nnz_bound, cudaStream_t st, double* Q = nullptr);
+  int64_t csr_nnz_ = 0;  // nonzeros of A the last CSR pass counted
   void compute_inverse(double* Li, cudaStream_t st);
   void factor(double* L, double* Li, cudaStream_t st);
   void refine_inverse(cudaStream_t st);

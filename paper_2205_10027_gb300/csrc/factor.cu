@@ -667,6 +667,22 @@ __global__ void __launch_bounds__(LEAF128_THREADS, 1) k_leaf128(double* Ablk, in
   if (tid == 0) *ld_part = tot;
 }
 
+// The leaf is launched with nearly all of an SM's shared memory (more than it uses), so that
+// no other block with shared memory is placed beside it: the concurrent tier-2 kernels and
+// the sparse products are FP64-bound, and FP64 instructions of a neighbour on the pivot
+// chain's sub-partition would delay every pivot.
+size_t leaf128_launch_smem() {
+  static const size_t v = [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return leaf128_smem();
+    const size_t reserve = optin > 16384 ? (size_t)optin - 8192 : 0;  // room for the static part
+    return std::max(leaf128_smem(), reserve);
+  }();
+  return v;
+}
+
 // out = sum of parts[0..n) in index order (one thread: n is at most a few hundred).
 __global__ void k_sum_parts(const double* parts, int n, const int* pd, double* out) {
   dep_wait();
@@ -728,6 +744,7 @@ struct Ctx {
   double* A;
   double* X;
   double* T;
+  double* T2;      // a second small-product scratch region of T (columns np - 256 ..), or null
   int64_t ld;
   double* ld_parts;
   int* pd;
@@ -780,14 +797,17 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
   if (!in_place) {
     launch_dependent(k_copy_block, std::min(s2, 1024), 256, 0, c.st, c.T, A21, ld, s2, s1, c.pd);
   }
-  // X21 = -X22 (L21 X11).  With a side stream and in-place tensor-core products, the first
-  // factor L21 X11 is formed into X21 on the side stream right away: it needs only L21 and
-  // X11, so it overlaps the trailing update and the whole right half.
+  // X21 = -X22 (L21 X11).  With a side stream, the first factor L21 X11 is formed on the side
+  // stream right away: it needs only L21 and X11, so it overlaps the trailing update and the
+  // whole right half.  In-place tensor-core products put it into X21; a small node whose
+  // right half is one leaf puts it into T2 (a node with a deeper right half would see its
+  // children's side products reuse T2 before its own last product reads it).
   const bool fork = in_place && c.side && c.side->st;
-  if (fork) {
+  const bool fork_small = !in_place && c.side && c.side->st && c.T2 && s2 == c.leaf;
+  if (fork || fork_small) {
     CUDA_CHECK(cudaEventRecord(c.side->fork, c.st));
     CUDA_CHECK(cudaStreamWaitEvent(c.side->st, c.side->fork, 0));
-    GemmArgs d = gemm_args(A21, ld, 0, X11, ld, 0, X21, ld, s2, s1, s1, 1.0, 0.0);
+    GemmArgs d = gemm_args(A21, ld, 0, X11, ld, 0, fork ? X21 : c.T2, ld, s2, s1, s1, 1.0, 0.0);
     d.krule = KR_LO_COL;
     d.flag = c.pd;
     (*c.gemm)(d, GemmRole::Inverse, c.side->st);
@@ -809,6 +829,15 @@ void chol_inv_rec(const Ctx& c, int o, int s) {
     (*c.gemm)(e, GemmRole::Inverse, c.st);
     return;
   }
+  if (fork_small) {
+    CUDA_CHECK(cudaEventRecord(c.side->join, c.side->st));
+    CUDA_CHECK(cudaStreamWaitEvent(c.st, c.side->join, 0));
+    GemmArgs e = gemm_args(X22, ld, 0, c.T2, ld, 0, X21, ld, s2, s1, s2, -1.0, 0.0);
+    e.krule = KR_HI_ROW;
+    e.flag = c.pd;
+    (*c.gemm)(e, GemmRole::Inverse, c.st);
+    return;
+  }
   GemmArgs d = gemm_args(A21, ld, 0, X11, ld, 0, c.T, ld, s2, s1, s1, 1.0, 0.0);
   d.krule = KR_LO_COL;
   d.flag = c.pd;
@@ -824,7 +853,7 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
                       double* logdet, const GemmFn& gemm, cudaStream_t st, bool split, LeafKind kind,
                       int panel, const SideStream* side) {
   const int leaf = kind == LeafKind::F64 ? NB : NB32;
-  const size_t smem = kind == LeafKind::F64Chol ? leaf128_smem()
+  const size_t smem = kind == LeafKind::F64Chol ? leaf128_launch_smem()
                       : kind == LeafKind::F32   ? leaf_smem(NB32, sizeof(float))
                                                 : leaf_smem(NB, sizeof(double));
   static std::once_flag once;  // not repeated inside a stream capture
@@ -835,11 +864,14 @@ void cholesky_inverse(double* A, double* X, int64_t ld, int np, double* T, doubl
     CUDA_CHECK(cudaFuncSetAttribute(k_leaf_chol_inv<double, NB, 4 * NB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)leaf_smem(NB, sizeof(double))));
-    CUDA_CHECK(cudaFuncSetAttribute(k_leaf128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf128_smem()));
+    CUDA_CHECK(cudaFuncSetAttribute(k_leaf128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf128_launch_smem()));
   });
   tri64_tables_once();
   CUDA_CHECK(cudaMemsetAsync(X, 0, sizeof(double) * ld * np, st));
-  Ctx c{split, kind, leaf, A, X, T, ld, ld_parts, pd, &gemm, st, smem, panel <= 0 ? side : nullptr};
+  // T2 = columns np - 256 .. np - 1 of T's first rows: disjoint from the top-left 256 x 256
+  // corner the main stream's small products use, when np >= 512
+  double* T2 = np >= 2 * kSmallGemm ? T + (np - kSmallGemm) : nullptr;
+  Ctx c{split, kind, leaf, A, X, T, T2, ld, ld_parts, pd, &gemm, st, smem, panel <= 0 ? side : nullptr};
   if (panel <= 0) {
     chol_inv_rec(c, 0, np);
   } else {
