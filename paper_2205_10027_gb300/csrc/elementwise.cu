@@ -444,7 +444,9 @@ __global__ void __launch_bounds__(RT) k_trace_pairs(const double* __restrict__ Q
   const int nt = np / 32;
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double s1 = 0.0, s2 = 0.0;
+  // s2 sums the diagonal tiles' products, s2o the off-diagonal tiles' (each standing for two
+  // symmetric pairs, doubled once at the end: one FP64 FMA per pair)
+  double s1 = 0.0, s2 = 0.0, s2o = 0.0;
   for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
     int bi, bj;
     tri_tile(tt, bi, bj);
@@ -460,15 +462,15 @@ __global__ void __launch_bounds__(RT) k_trace_pairs(const double* __restrict__ Q
       const int64_t i = (int64_t)bi * 32 + r, j = (int64_t)bj * 32 + tx;
       if (bi == bj) {
         // Q_ij Q_ji over the whole diagonal tile, each unordered pair twice as in the sum
-        s2 += a[r][tx] * a[tx][r];
+        s2 = fma(a[r][tx], a[tx][r], s2);
         if (i == j) s1 += a[r][tx];
       } else {
-        s2 += 2.0 * a[r][tx] * b[tx][r];
+        s2o = fma(a[r][tx], b[tx][r], s2o);
       }
     }
   }
   const double v0 = block_sum(s1, red);
-  const double v1 = block_sum(s2, red);
+  const double v1 = block_sum(fma(2.0, s2o, s2), red);
   if (threadIdx.x == 0) {
     parts[(int64_t)blockIdx.x * 2] = v0;
     parts[(int64_t)blockIdx.x * 2 + 1] = v1;
